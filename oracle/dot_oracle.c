@@ -1,0 +1,254 @@
+/*
+ * dot_oracle.c -- plain, slow, obviously correct CPU reference for the
+ * multi-limb add / sub / mul of "Leveraging SIMD for Accelerating
+ * Large-number Arithmetic" (DigitsOnTurbo).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path links, loads or
+ * calls this file: only the test suite, the package's smoke check and the
+ * bench's CPU-baseline leg do.  It shares no code, header, table or constant
+ * with the CUDA library; it sees only the raw limb arrays.
+ *
+ * Number representation (Sec. 2.1, Table 2): an m-limb operand is
+ * A = sum_{i<m} A_i X^i with X = 2^k; here k = 32, limbs little-endian
+ * (A_0 first), one operand per row of a [batch][m] array.
+ *
+ * What each function computes (the plain definitions the method reaches):
+ *   add : S + c_out X^m = A + B                  (Theorem 1, Sec. 3.1)
+ *   sub : D - b_out X^m = A - B, b_out in {0,1}  (Sec. 3.1, "Subtraction")
+ *   mul : P = A * B as exactly 2m limbs          (Theorem 2, Sec. 3.2)
+ * The add/sub loops are the textbook S_i = A_i + B_i + C_{i-1} recurrence
+ * (Sec. 2.2 and Alg. 3, MPN-ADD-M) with 64-bit intermediates; the product is
+ * the ROW-wise schoolbook (operand scanning), deliberately not the column form
+ * the GPU uses.  oracle_mul_vnc is a separate restatement of Alg. 2
+ * (vertical-and-crosswise, Phases 1-5 in the paper's order) kept to check the
+ * paper's own column algorithm; it is not the parity target.
+ *
+ * Readings where the paper is silent (listed in the design notes):
+ *   - limbs are 32-bit (the paper uses 64 / 52); results are radix-free;
+ *   - the product has exactly 2m limbs; Alg. 2's "prepend carry" branch is
+ *     unreachable for A, B < X^m, so oracle_mul_vnc reports it as an error;
+ *   - subtraction with A < B wraps modulo X^m and returns borrow 1;
+ *   - there is no carry-in (Alg. 1 starts with c_out = 0).
+ *
+ * All functions return 0 on success, -1 on a bad argument.
+ */
+#include <stdint.h>
+#include <stddef.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- add: S_i = (A_i + B_i + c_i) mod X, c_{i+1} = floor(.../X) ---------- */
+static void add_one(const uint32_t *a, const uint32_t *b, uint32_t *s,
+                    uint32_t *carry, size_t m)
+{
+    uint64_t c = 0;
+    for (size_t i = 0; i < m; ++i) {
+        uint64_t t = (uint64_t)a[i] + (uint64_t)b[i] + c;
+        s[i] = (uint32_t)t;
+        c = t >> 32;
+    }
+    *carry = (uint32_t)c;
+}
+
+/* ---- sub: D_i = (A_i - B_i - br_i) mod X, br_{i+1} = [A_i < B_i + br_i] -- */
+static void sub_one(const uint32_t *a, const uint32_t *b, uint32_t *d,
+                    uint32_t *borrow, size_t m)
+{
+    uint64_t br = 0;
+    for (size_t i = 0; i < m; ++i) {
+        /* two's-complement 64-bit difference: bit 63 is set iff it went negative */
+        uint64_t t = (uint64_t)a[i] - (uint64_t)b[i] - br;
+        d[i] = (uint32_t)t;
+        br = t >> 63;
+    }
+    *borrow = (uint32_t)br;
+}
+
+/* ---- mul: row-wise schoolbook into 2m limbs ------------------------------ */
+static void mul_one(const uint32_t *a, const uint32_t *b, uint32_t *p, size_t m)
+{
+    for (size_t i = 0; i < 2 * m; ++i) p[i] = 0;
+    for (size_t i = 0; i < m; ++i) {
+        uint64_t c = 0;
+        for (size_t j = 0; j < m; ++j) {
+            /* (2^32-1)^2 + 2 (2^32-1) = 2^64 - 1: never overflows */
+            uint64_t t = (uint64_t)a[i] * (uint64_t)b[j] + (uint64_t)p[i + j] + c;
+            p[i + j] = (uint32_t)t;
+            c = t >> 32;
+        }
+        p[i + m] = (uint32_t)c;
+    }
+}
+
+int oracle_add(const uint32_t *a, const uint32_t *b, uint32_t *s, uint32_t *carry,
+               size_t m, size_t batch)
+{
+    if (batch && (!carry || (m && (!a || !b || !s)))) return -1;
+    for (size_t k = 0; k < batch; ++k)
+        add_one(a + k * m, b + k * m, s + k * m, carry + k, m);
+    return 0;
+}
+
+int oracle_sub(const uint32_t *a, const uint32_t *b, uint32_t *d, uint32_t *borrow,
+               size_t m, size_t batch)
+{
+    if (batch && (!borrow || (m && (!a || !b || !d)))) return -1;
+    for (size_t k = 0; k < batch; ++k)
+        sub_one(a + k * m, b + k * m, d + k * m, borrow + k, m);
+    return 0;
+}
+
+int oracle_mul(const uint32_t *a, const uint32_t *b, uint32_t *p, size_t m, size_t batch)
+{
+    if (batch && m && (!a || !b || !p)) return -1;
+    for (size_t k = 0; k < batch; ++k)
+        mul_one(a + k * m, b + k * m, p + 2 * k * m, m);
+    return 0;
+}
+
+/* ---- ragged: op i has off[i+1]-off[i] limbs; products at poff[i] --------- */
+int oracle_add_ragged(const uint32_t *a, const uint32_t *b, uint32_t *s, uint32_t *carry,
+                      const uint64_t *off, size_t batch)
+{
+    if (batch && (!off || !carry)) return -1;
+    for (size_t k = 0; k < batch; ++k) {
+        if (off[k + 1] < off[k]) return -1;
+        add_one(a + off[k], b + off[k], s + off[k], carry + k, (size_t)(off[k + 1] - off[k]));
+    }
+    return 0;
+}
+
+int oracle_sub_ragged(const uint32_t *a, const uint32_t *b, uint32_t *d, uint32_t *borrow,
+                      const uint64_t *off, size_t batch)
+{
+    if (batch && (!off || !borrow)) return -1;
+    for (size_t k = 0; k < batch; ++k) {
+        if (off[k + 1] < off[k]) return -1;
+        sub_one(a + off[k], b + off[k], d + off[k], borrow + k, (size_t)(off[k + 1] - off[k]));
+    }
+    return 0;
+}
+
+int oracle_mul_ragged(const uint32_t *a, const uint32_t *b, uint32_t *p,
+                      const uint64_t *off, const uint64_t *poff, size_t batch)
+{
+    if (batch && (!off || !poff)) return -1;
+    for (size_t k = 0; k < batch; ++k) {
+        if (off[k + 1] < off[k]) return -1;
+        mul_one(a + off[k], b + off[k], p + poff[k], (size_t)(off[k + 1] - off[k]));
+    }
+    return 0;
+}
+
+/* ---- mixed ragged: op[i] in {0 add, 1 sub, 2 mul}; carry[i] = carry/borrow
+ *      of an add/sub, 0 for a product ---------------------------------------- */
+int oracle_mixed(const uint32_t *op, const uint32_t *mlimbs, const uint64_t *a_off,
+                 const uint64_t *b_off, const uint64_t *r_off, size_t nops,
+                 const uint32_t *a, const uint32_t *b, uint32_t *r, uint32_t *carry)
+{
+    if (nops && (!op || !mlimbs || !a_off || !b_off || !r_off || !carry)) return -1;
+    for (size_t i = 0; i < nops; ++i) {
+        size_t m = mlimbs[i];
+        switch (op[i]) {
+        case 0: add_one(a + a_off[i], b + b_off[i], r + r_off[i], carry + i, m); break;
+        case 1: sub_one(a + a_off[i], b + b_off[i], r + r_off[i], carry + i, m); break;
+        case 2: mul_one(a + a_off[i], b + b_off[i], r + r_off[i], m); carry[i] = 0; break;
+        default: return -1;
+        }
+    }
+    return 0;
+}
+
+/* ---- Alg. 2 (DoT-Mul-Words) restated, Phases 1-5 in the paper's order ----
+ * Phase 1 gathers, for each column c = 0..2m-2 and each (i, j) with i+j = c
+ * (i ascending), A_i into M_a and B_j into M_b.  Phase 2 forms every partial
+ * product against a zero accumulator, split into a low and a high k-bit half.
+ * Phase 3 walks the columns with num_pairs = min(c+1, m, 2m-1-c), adding the
+ * low halves into col[c] and the high halves into col[c+1].  Phase 4 copies
+ * the column values into P, and Phase 5 is one sequential carry pass over the
+ * 2m entries.  Column values are kept in 64 bits: col < 2m * 2^32.
+ * The SIMD chunking (step w) of Phase 2 does not change any value and is not
+ * reproduced.  Returns -2 if Phase 5 leaves a nonzero carry (the "prepend"
+ * branch, unreachable for m-limb inputs). */
+static int vnc_one(const uint32_t *A, const uint32_t *B, uint32_t *P, size_t m,
+                   uint32_t *Ma, uint32_t *Mb, uint32_t *Plo, uint32_t *Phi,
+                   uint64_t *col)
+{
+    const size_t mm = m * m;
+    size_t idx_a = 0, idx_b = 0;
+    /* Phase 1 */
+    for (size_t c = 0; c + 1 < 2 * m; ++c) {
+        for (size_t i = 0; i <= c; ++i) {
+            size_t j = c - i;
+            if (i >= m || j >= m) continue;
+            Ma[idx_a++] = A[i];
+            Mb[idx_b++] = B[j];
+        }
+    }
+    if (idx_a != mm || idx_b != mm) return -3;
+    /* Phase 2 */
+    for (size_t t = 0; t < mm; ++t) {
+        uint64_t prod = (uint64_t)Ma[t] * (uint64_t)Mb[t];
+        Plo[t] = (uint32_t)prod;
+        Phi[t] = (uint32_t)(prod >> 32);
+    }
+    /* Phase 3 */
+    for (size_t c = 0; c < 2 * m; ++c) col[c] = 0;
+    size_t idx = 0;
+    for (size_t c = 0; c + 1 < 2 * m; ++c) {
+        size_t num_pairs = c + 1;
+        if (m < num_pairs) num_pairs = m;
+        if (2 * m - 1 - c < num_pairs) num_pairs = 2 * m - 1 - c;
+        for (size_t q = 0; q < num_pairs; ++q) {
+            size_t t = idx + q;
+            col[c] += Plo[t];
+            col[c + 1] += Phi[t];
+        }
+        idx += num_pairs;
+    }
+    /* Phase 4 + Phase 5 */
+    uint64_t carry = 0;
+    for (size_t c = 0; c < 2 * m; ++c) {
+        uint64_t v = col[c] + carry;
+        carry = v >> 32;
+        P[c] = (uint32_t)v;
+    }
+    return carry ? -2 : 0;
+}
+
+int oracle_mul_vnc(const uint32_t *a, const uint32_t *b, uint32_t *p, size_t m, size_t batch)
+{
+    if (batch && m && (!a || !b || !p)) return -1;
+    if (!m || !batch) return 0;
+    size_t mm = m * m;
+    uint32_t *Ma = malloc(mm * sizeof *Ma), *Mb = malloc(mm * sizeof *Mb);
+    uint32_t *Plo = malloc(mm * sizeof *Plo), *Phi = malloc(mm * sizeof *Phi);
+    uint64_t *col = malloc(2 * m * sizeof *col);
+    int rc = (Ma && Mb && Plo && Phi && col) ? 0 : -4;
+    for (size_t k = 0; k < batch && rc == 0; ++k)
+        rc = vnc_one(a + k * m, b + k * m, p + 2 * k * m, m, Ma, Mb, Plo, Phi, col);
+    free(Ma); free(Mb); free(Plo); free(Phi); free(col);
+    return rc;
+}
+
+/* The Phase 1 gather order of Alg. 2 as (i, j) index pairs, and the number of
+ * pairs per column, for the structural checks of the m = 5 worked example.
+ * ia, jb hold m*m entries; ncol holds 2m-1 entries. */
+int oracle_vnc_pairs(size_t m, int32_t *ia, int32_t *jb, int32_t *ncol)
+{
+    if (!m || !ia || !jb || !ncol) return -1;
+    size_t t = 0;
+    for (size_t c = 0; c + 1 < 2 * m; ++c) {
+        int32_t n = 0;
+        for (size_t i = 0; i <= c; ++i) {
+            size_t j = c - i;
+            if (i >= m || j >= m) continue;
+            ia[t] = (int32_t)i;
+            jb[t] = (int32_t)j;
+            ++t;
+            ++n;
+        }
+        ncol[c] = n;
+    }
+    return t == m * m ? 0 : -3;
+}
