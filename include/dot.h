@@ -1,0 +1,211 @@
+/*
+ * dot.h -- C ABI of libdot, a GB300 (sm_103a) library for exact multi-limb
+ * unsigned integer add, subtract and multiply, after "Leveraging SIMD for
+ * Accelerating Large-number Arithmetic" (DigitsOnTurbo, DoT).
+ *
+ * Number format (Sec. 2.1, Table 2).  An operand of m limbs is the integer
+ *     A = sum_{i<m} A_i X^i,  X = 2^32,  0 <= A_i < X,
+ * stored little-endian as uint32_t[m] (A_0 first).  A batch of equal-size
+ * operands is row-major uint32_t[batch][m]; a ragged batch is packed
+ * back-to-back with an offsets array (CSR style).
+ *
+ * Memory.  Unless a function says "host", every pointer is a device pointer
+ * (cudaMalloc, torch tensors, ...) owned by the caller; the library never
+ * frees it.  A dot_ctx_t owns all scratch (look-back tile states, counters,
+ * the sticky status word, staging buffers, captured graphs).  Calls are
+ * asynchronous on `stream` (a cudaStream_t passed as void*, NULL = legacy
+ * default stream).  Calls that share a ctx must be ordered on one stream:
+ * two in flight at once on different streams race on the ctx scratch.
+ *
+ * Aliasing.  For add/sub the result may alias an operand exactly (in-place,
+ * s == a or s == b) but must not overlap it partially.  A product must not
+ * overlap its operands.  Detectable violations give DOT_EINVAL.
+ *
+ * Errors.  Argument errors are returned synchronously before any launch and
+ * nothing is written.  Launch failures give DOT_ECUDA.  Device-side errors
+ * (a bounded wait that ran out) are recorded in the ctx and returned, and
+ * cleared, by dot_ctx_check.  The library never exits, aborts or traps.
+ *
+ * There is no CPU fallback: every entry point runs its work on the GPU.
+ */
+#ifndef DOT_H
+#define DOT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define DOT_API __attribute__((visibility("default")))
+#else
+#define DOT_API
+#endif
+
+#define DOT_ABI_VERSION 1
+
+typedef enum dot_status {
+    DOT_OK = 0,
+    DOT_EINVAL = 1,        /* bad argument: null pointer, overlap, size overflow */
+    DOT_ECUDA = 2,         /* a CUDA runtime call or kernel launch failed        */
+    DOT_ENOMEM = 3,        /* scratch allocation failed                          */
+    DOT_ETIMEOUT = 4,      /* a bounded device-side wait ran out (see check)     */
+    DOT_EUNSUPPORTED = 5   /* size or mode outside what the kernels implement   */
+} dot_status_t;
+
+/* operation codes of mixed ragged descriptors */
+enum { DOT_OP_ADD = 0, DOT_OP_SUB = 1, DOT_OP_MUL = 2 };
+
+/* Largest operand (limbs) of the column-sum multiply kernels. */
+#define DOT_MUL_MAX_LIMBS 512
+
+typedef struct dot_ctx *dot_ctx_t;
+typedef void *dot_stream_t;   /* cudaStream_t */
+
+/* ---------------------------------------------------------------- ctx --- */
+
+/* Create a context on CUDA device `device`; allocates its scratch there.
+ * *out is set only on DOT_OK.  Errors: DOT_EINVAL (out NULL), DOT_ECUDA,
+ * DOT_ENOMEM. */
+DOT_API dot_status_t dot_ctx_create(dot_ctx_t *out, int device);
+
+/* Free a context and its scratch (synchronises its device).  NULL is a no-op. */
+DOT_API void dot_ctx_destroy(dot_ctx_t ctx);
+
+/* Synchronise `stream`, then return and clear the ctx's sticky device status
+ * (DOT_OK, or DOT_ETIMEOUT if a bounded look-back wait ran out since the last
+ * check), or DOT_ECUDA if the stream reports an error. */
+DOT_API dot_status_t dot_ctx_check(dot_ctx_t ctx, dot_stream_t stream);
+
+/* Upper bound, in nanoseconds, on any single device-side wait of this ctx
+ * (default 2e9 = 2 s).  After it a waiting thread block records DOT_ETIMEOUT,
+ * treats the missing carry as 0 and finishes, so every launch terminates. */
+DOT_API dot_status_t dot_ctx_set_wait_limit(dot_ctx_t ctx, uint64_t nanoseconds);
+
+/* Static description of a status code; never NULL. */
+DOT_API const char *dot_status_str(dot_status_t status);
+
+/* DOT_ABI_VERSION of the loaded library. */
+DOT_API int dot_abi_version(void);
+
+/* ------------------------------------------------------- add / subtract --- */
+
+/* Batched addition, Alg. 1 (DoT-Add-Words) and Theorem 1 (Sec. 3.1):
+ * for each row k < batch,  s[k] + carry_out[k] * X^m = a[k] + b[k].
+ * a, b, s: uint32_t[batch][m]; carry_out: uint32_t[batch], each 0 or 1.
+ * Operands longer than one thread block's tile are chained across blocks by
+ * decoupled look-back.  m == 0 gives carry 0; batch == 0 is a no-op. */
+DOT_API dot_status_t dot_add(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b,
+                             uint32_t *s, uint32_t *carry_out, size_t m, size_t batch,
+                             dot_stream_t stream);
+
+/* Batched subtraction, the borrow mirror of Alg. 1 (Sec. 3.1, "Subtraction"):
+ * d[k] - borrow_out[k] * X^m = a[k] - b[k], borrow_out[k] = 1 iff a[k] < b[k]
+ * (the difference then wraps modulo X^m).  Layout as dot_add. */
+DOT_API dot_status_t dot_sub(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b,
+                             uint32_t *d, uint32_t *borrow_out, size_t m, size_t batch,
+                             dot_stream_t stream);
+
+/* Ragged addition / subtraction: op k has m_k = off[k+1] - off[k] limbs at
+ * a + off[k], b + off[k], written to s + off[k]; carry/borrow to [k].
+ * off: device uint64_t[batch + 1], non-decreasing (checked on the device:
+ * a decreasing entry records DOT_EINVAL in the ctx and the op is skipped). */
+DOT_API dot_status_t dot_add_ragged(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b,
+                                    uint32_t *s, uint32_t *carry_out, const uint64_t *off,
+                                    size_t batch, dot_stream_t stream);
+DOT_API dot_status_t dot_sub_ragged(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b,
+                                    uint32_t *d, uint32_t *borrow_out, const uint64_t *off,
+                                    size_t batch, dot_stream_t stream);
+
+/* --------------------------------------------------------------- multiply --- */
+
+/* Batched product, Alg. 2 (DoT-Mul-Words) and Theorem 2 (Sec. 3.2):
+ * p[k] = a[k] * b[k] as exactly 2m limbs.  a, b: uint32_t[batch][m];
+ * p: uint32_t[batch][2m], must not overlap a or b.  Column sums of
+ * independent 32x32->64 partial products, then one exact carry-resolution
+ * pass.  1 <= m <= DOT_MUL_MAX_LIMBS, else DOT_EUNSUPPORTED (m == 0: no-op). */
+DOT_API dot_status_t dot_mul(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b,
+                             uint32_t *p, size_t m, size_t batch, dot_stream_t stream);
+
+/* Ragged product: op k has m_k = off[k+1] - off[k] limbs (<= DOT_MUL_MAX_LIMBS,
+ * larger ops record DOT_EUNSUPPORTED in the ctx and are skipped); its 2 m_k
+ * product limbs go to p + poff[k].  off, poff: device uint64_t[batch + 1]. */
+DOT_API dot_status_t dot_mul_ragged(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b,
+                                    uint32_t *p, const uint64_t *off, const uint64_t *poff,
+                                    size_t batch, dot_stream_t stream);
+
+/* ------------------------------------------------------------ mixed batch --- */
+
+/* One operation of a mixed ragged batch (32 bytes).  Operand a occupies
+ * a[a_off .. a_off + m), operand b occupies b[b_off .. b_off + m); the result
+ * (m limbs for add/sub, 2m for mul) goes to r[r_off ..]; the carry/borrow of
+ * descriptor i goes to carry[i] (0 for a product). */
+typedef struct dot_desc {
+    uint32_t op;      /* DOT_OP_ADD, DOT_OP_SUB or DOT_OP_MUL */
+    uint32_t m;       /* limbs of each operand */
+    uint64_t a_off;
+    uint64_t b_off;
+    uint64_t r_off;
+} dot_desc_t;
+
+/* Mixed ragged batch of add/sub/mul operations (device descriptors).
+ * The library sorts the ops into size buckets on the device and runs them in
+ * one persistent kernel replayed from a captured CUDA graph, with tile shapes
+ * from its tuning table.  Mul ops need m <= DOT_MUL_MAX_LIMBS; larger ones and
+ * unknown op codes record DOT_EUNSUPPORTED / DOT_EINVAL and are skipped. */
+DOT_API dot_status_t dot_mixed_ragged(dot_ctx_t ctx, const dot_desc_t *desc, size_t nops,
+                                      const uint32_t *a, const uint32_t *b, uint32_t *r,
+                                      uint32_t *carry, dot_stream_t stream);
+
+/* ---------------------------------------------------- host-buffer variants --- */
+
+/* Same results as dot_add / dot_sub / dot_mul, but a, b and the outputs are
+ * HOST pointers (pinned memory gives asynchronous copies; pageable memory
+ * works but is staged by the driver).  The library copies the operands into
+ * ctx-owned device staging buffers chunk by chunk, computes, and copies the
+ * results back, overlapping the copies of one chunk with the compute of
+ * another.  Returns after enqueueing; the host outputs are valid once
+ * `stream` has been synchronised (dot_ctx_check does that). */
+DOT_API dot_status_t dot_add_host(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b,
+                                  uint32_t *s, uint32_t *carry_out, size_t m, size_t batch,
+                                  dot_stream_t stream);
+DOT_API dot_status_t dot_sub_host(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b,
+                                  uint32_t *d, uint32_t *borrow_out, size_t m, size_t batch,
+                                  dot_stream_t stream);
+DOT_API dot_status_t dot_mul_host(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b,
+                                  uint32_t *p, size_t m, size_t batch, dot_stream_t stream);
+
+/* ------------------------------------------------------- introspection --- */
+
+/* The launch plan the library uses for one batched call (host logic only,
+ * needs no GPU).  op is DOT_OP_ADD / SUB / MUL. */
+typedef struct dot_plan {
+    int kernel;          /* 1 warp-segmented add/sub, 2 tiled add/sub with
+                            look-back, 3 column-sum multiply, 0 nothing to do */
+    int seg_limbs;       /* limbs per thread segment (vector width)          */
+    int lanes_per_op;    /* threads that cooperate on one op (<= 32), or the
+                            threads of one tile for kernel 2                  */
+    int chunks;          /* segments per thread                              */
+    uint64_t tile_limbs; /* limbs per tile (kernel 2)                        */
+    uint64_t tiles;      /* tiles per op (kernel 2)                          */
+    uint64_t m_pad;      /* padded operand length (kernel 3)                 */
+} dot_plan_t;
+
+DOT_API dot_status_t dot_plan_batched(int op, size_t m, size_t batch, int vector_ok,
+                                      dot_plan_t *out);
+
+/* ----------------------------------------------------------- debug hook --- */
+
+/* Test hook for the bounded waits: while set, the next dot_add / dot_sub on
+ * this ctx that uses look-back never publishes the carry state of tile
+ * `tile` of op 0, so its successor's wait runs out (DOT_ETIMEOUT at the next
+ * dot_ctx_check; results of that op are then unspecified).  -1 clears it. */
+DOT_API dot_status_t dot_debug_skip_publish(dot_ctx_t ctx, int64_t tile);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DOT_H */

@@ -1,0 +1,453 @@
+// dot_addsub.cu -- batched and ragged multi-limb addition / subtraction.
+//
+// DoT addition (Alg. 1, Theorem 1, Sec. 3.1) re-shaped for a GPU:
+//  * Phase 1 (independent limb adds) and Phase 2 (generate / propagate bits)
+//    run on each thread's segment of 1 or 4 limbs, loaded with 128-bit
+//    coalesced loads.
+//  * Alg. 1's sequential chain of c_out between SIMD chunks is replaced by a
+//    carry-lookahead: segment (g, p) bits are gathered with __ballot_sync
+//    and resolved with the same mask identity Phase 4 uses,
+//    carries = ((G << 1 | c_in) + P) ^ P.
+//  * Operands longer than one thread block's tile are chained across blocks
+//    by decoupled look-back over per-tile states in global memory.
+//  * Phases 3-4 (adding the carries back) happen in registers before the
+//    streaming store.
+// Subtraction is the same with borrows (Sec. 3.1, "Subtraction").
+#include "dot_internal.cuh"
+#include "dot_plan.h"
+
+#define WARP_KERNEL_THREADS 256
+
+// --------------------------------------------------------------- loading
+template <int SEG>
+__device__ __forceinline__ void load_seg(const uint32_t *p, uint32_t (&v)[SEG])
+{
+    if constexpr (SEG == 4) {
+        const uint4 q = ld_stream4(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < SEG; ++i) v[i] = ld_stream1(p + i);
+    }
+}
+
+template <int SEG>
+__device__ __forceinline__ void store_seg(uint32_t *p, const uint32_t (&v)[SEG])
+{
+    if constexpr (SEG == 4) {
+        st_stream4(p, make_uint4(v[0], v[1], v[2], v[3]));
+    } else {
+#pragma unroll
+        for (int i = 0; i < SEG; ++i) st_stream1(p + i, v[i]);
+    }
+}
+
+// ======================================================= warp kernel (1)
+// Each op lies inside one warp: runs of `lpo` lanes per op (several ops per
+// warp when the op has at most 16 segments), or all 32 lanes and up to NCH
+// chunks of 32 segments chained through the warp's carry-out.  U independent
+// op groups are loaded before any is resolved, to keep enough bytes in flight.
+template <bool SUB, int SEG, int NCH, int U>
+__global__ void __launch_bounds__(WARP_KERNEL_THREADS)
+addsub_warp_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint32_t *cout,
+                   size_t m, size_t batch, int lpo, int nch)
+{
+    const int lane = (int)lane_id();
+    const int opw = 32 / lpo;
+    const int grp = lane / lpo;
+    const int rel = lane - grp * lpo;
+    const bool lane_on = grp < opw;
+    const uint32_t smask = run_start_mask(lpo), tmask = run_top_mask(lpo);
+    const size_t Q = (m + SEG - 1) / SEG;
+    const int last_chunk = (int)((Q - 1) / (size_t)lpo);
+    const int last_rel = (int)((Q - 1) % (size_t)lpo);
+    const size_t warp_global = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const size_t nwarps = ((size_t)gridDim.x * blockDim.x) >> 5;
+    const size_t per_iter = (size_t)opw * U;
+
+    for (size_t base = warp_global * per_iter; base < batch; base += nwarps * per_iter) {
+        uint32_t x[U][NCH][SEG], y[U][NCH][SEG];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const size_t op = base + (size_t)u * opw + grp;
+#pragma unroll
+            for (int j = 0; j < NCH; ++j) {
+                const size_t q = (size_t)j * lpo + rel;
+                if (lane_on && op < batch && j < nch && q < Q) {
+                    load_seg<SEG>(a + op * m + q * SEG, x[u][j]);
+                    load_seg<SEG>(b + op * m + q * SEG, y[u][j]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < SEG; ++i) x[u][j][i] = y[u][j][i] = 0;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const size_t op = base + (size_t)u * opw + grp;
+            const bool op_on = lane_on && op < batch;
+            uint32_t cin = 0;
+#pragma unroll
+            for (int j = 0; j < NCH; ++j) {
+                if (j >= nch) break;
+                const size_t q = (size_t)j * lpo + rel;
+                const bool on = op_on && q < Q;
+                Segment<SUB, SEG> sg;
+                sg.phase12(x[u][j], y[u][j]);
+                WarpCarry wc;
+                wc.resolve(on ? sg.g() : 0u, on ? sg.p() : 0u, rel == 0 ? cin : 0u, smask, tmask);
+                const uint32_t c = wc.carry_in(lane);
+                sg.apply(c);
+                if (on) store_seg<SEG>(s + op * m + q * SEG, sg.r);
+                if (j == last_chunk) {
+                    if (on && rel == last_rel) cout[op] = sg.cout(c);
+                } else {
+                    cin = wc.carry_out(31);   // lpo == 32 whenever there are several chunks
+                }
+            }
+        }
+    }
+}
+
+// ================================================= tiled kernel (2) + look-back
+// A tile is DOT_TILE_THREADS threads x NCH chunks x SEG limbs of one op.  Tiles
+// are taken in ticket order (atomic counter), so every tile's predecessor in
+// its op has already been taken by a running block: the look-back wait always
+// ends.  Each tile publishes its carry state (epoch-tagged): INCLUSIVE as soon
+// as its own aggregate decides the carry-out (generate or kill), PROPAGATE
+// otherwise, then INCLUSIVE once its carry-in is known.
+__device__ uint32_t lookback_carry(const LookbackArgs &lb, const unsigned long long *st_op,
+                                   long long t, unsigned long long epoch, int lane)
+{
+    long long j_hi = t - 1;
+    uint64_t t0 = 0;
+    bool timing = false;
+    for (;;) {
+        const long long j = j_hi - lane;
+        uint32_t code = LB_INCL0;   // before the op's first tile: carry 0
+        if (j >= 0) {
+            const unsigned long long w = ld_acquire_u64(st_op + j);
+            code = ((w >> 2) == epoch) ? (uint32_t)(w & 3ull) : (uint32_t)LB_EMPTY;
+        }
+        const uint32_t incl = __ballot_sync(DOT_FULL, code >= LB_INCL0);
+        const uint32_t empty = __ballot_sync(DOT_FULL, code == LB_EMPTY);
+        const uint32_t nearer = incl ? ((incl & (0u - incl)) - 1u) : DOT_FULL;
+        if ((empty & nearer) == 0) {
+            if (incl) {
+                const int L = __ffs(incl) - 1;
+                return __shfl_sync(DOT_FULL, code, L) & 1u;
+            }
+            j_hi -= 32;   // 32 propagating predecessors: keep walking back
+            continue;
+        }
+        // a nearer predecessor has not published yet: wait (bounded)
+        uint64_t now = 0;
+        if (lane == 0) now = globaltimer_ns();
+        now = __shfl_sync(DOT_FULL, now, 0);
+        if (!timing) {
+            t0 = now;
+            timing = true;
+        } else if (now - t0 > lb.wait_limit_ns) {
+            if (lane == 0) record_status(lb.status, DOT_ETIMEOUT);
+            return 0;
+        }
+        __nanosleep(100);
+    }
+}
+
+template <bool SUB, int SEG, int NCH>
+__global__ void __launch_bounds__(DOT_TILE_THREADS)
+addsub_tile_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint32_t *cout,
+                   size_t m, size_t batch, unsigned long long tiles_per_op, LookbackArgs lb)
+{
+    constexpr int WARPS = DOT_TILE_THREADS / 32;
+    constexpr unsigned long long TILE = (unsigned long long)DOT_TILE_THREADS * SEG * NCH;
+    constexpr int WARP_LIMBS = 32 * SEG * NCH;
+    __shared__ unsigned long long s_ticket;
+    __shared__ uint32_t s_wagg[WARPS];
+    __shared__ uint32_t s_cin;
+    const int lane = (int)lane_id();
+    const int warp = (int)(threadIdx.x >> 5);
+    const unsigned long long epoch = lb.counters[2];
+    const unsigned long long total = (unsigned long long)batch * tiles_per_op;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_ticket = atomicAdd(&lb.counters[0], 1ull);
+        __syncthreads();
+        const unsigned long long ticket = s_ticket;
+        if (ticket >= total) break;
+        const unsigned long long op = ticket / tiles_per_op;
+        const unsigned long long t = ticket - op * tiles_per_op;
+        const size_t wbase = (size_t)(t * TILE) + (size_t)warp * WARP_LIMBS;
+        const uint32_t *ar = a + op * m;
+        const uint32_t *br = b + op * m;
+        uint32_t *sr = s + op * m;
+
+        uint32_t x[NCH][SEG], y[NCH][SEG];
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) {
+            const size_t li = wbase + ((size_t)j * 32 + lane) * SEG;
+            if (li < m) {
+                load_seg<SEG>(ar + li, x[j]);
+                load_seg<SEG>(br + li, y[j]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < SEG; ++i) x[j][i] = y[j][i] = 0;
+            }
+        }
+        Segment<SUB, SEG> sg[NCH];
+        uint32_t G[NCH], P[NCH];
+        uint32_t wg = 0, wp = 1;   // warp aggregate, composed chunk by chunk
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) {
+            sg[j].phase12(x[j], y[j]);
+            const size_t li = wbase + ((size_t)j * 32 + lane) * SEG;
+            const bool on = li < m;
+            WarpCarry wc;
+            wc.resolve(on ? sg[j].g() : 0u, on ? sg[j].p() : 0u, 0u, 1u, 0x80000000u);
+            G[j] = wc.G;
+            P[j] = wc.P;
+            gp_compose(wg, wp, wc.carry_out(31), (uint32_t)(wc.P == DOT_FULL));
+        }
+        if (lane == 0) s_wagg[warp] = wg | (wp << 1);
+        __syncthreads();
+
+        if (warp == 0) {
+            uint32_t tg = 0, tp = 1;
+#pragma unroll
+            for (int w = 0; w < WARPS; ++w) gp_compose(tg, tp, s_wagg[w] & 1u, s_wagg[w] >> 1);
+            unsigned long long *st_op = lb.state + (ticket - t);
+            const bool skip = lb.skip_tile >= 0 && op == 0 && (long long)t == lb.skip_tile;
+            uint32_t cin_tile = 0;
+            if (t == 0) {
+                if (lane == 0 && !skip)
+                    st_release_u64(st_op, (epoch << 2) | (tg ? LB_INCL1 : LB_INCL0));
+            } else {
+                if (lane == 0 && !skip)
+                    st_release_u64(st_op + t, (epoch << 2) | (tp ? LB_PROP : (tg ? LB_INCL1 : LB_INCL0)));
+                cin_tile = lookback_carry(lb, st_op, (long long)t, epoch, lane);
+                if (tp && lane == 0 && !skip)
+                    st_release_u64(st_op + t, (epoch << 2) | (cin_tile ? LB_INCL1 : LB_INCL0));
+            }
+            if (lane == 0) s_cin = cin_tile;
+        }
+        __syncthreads();
+
+        // carry into this warp: the tile carry-in passed through the warps below
+        uint32_t c = s_cin;
+        for (int w = 0; w < warp; ++w) {
+            uint32_t g = s_wagg[w] & 1u, p = s_wagg[w] >> 1;
+            c = g | (p & c);
+        }
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) {
+            const size_t li = wbase + ((size_t)j * 32 + lane) * SEG;
+            const uint32_t Pm = P[j] & 0x7fffffffu;
+            const uint32_t C = (((G[j] << 1) | c) + Pm) ^ Pm;
+            const uint32_t ci = (C >> lane) & 1u;
+            sg[j].apply(ci);
+            if (li < m) {
+                store_seg<SEG>(sr + li, sg[j].r);
+                if (li + SEG >= m && t == tiles_per_op - 1) cout[op] = sg[j].cout(ci);
+            }
+            c = ((G[j] >> 31) | ((P[j] >> 31) & (C >> 31))) & 1u;
+        }
+        __syncthreads();
+    }
+    // the last block out resets the ticket counter and advances the epoch
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned long long prev = atomicAdd(&lb.counters[1], 1ull);
+        if (prev == gridDim.x - 1) {
+            lb.counters[0] = 0;
+            lb.counters[1] = 0;
+            __threadfence();
+            lb.counters[2] = epoch + 1;
+        }
+    }
+}
+
+// ===================================================== ragged kernel (one warp per op)
+// Op k has off[k+1] - off[k] limbs.  The warp walks its op in groups of
+// 4 x 32 limbs (loads first), resolving each 32-limb chunk with the ballot
+// lookahead and passing the chunk carry-out on -- Alg. 1's chunk loop with
+// w = 32 lanes.
+template <bool SUB>
+__global__ void __launch_bounds__(WARP_KERNEL_THREADS)
+addsub_ragged_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint32_t *cout,
+                     const uint64_t *off, size_t batch, uint32_t *status)
+{
+    constexpr int K = 4;
+    const int lane = (int)lane_id();
+    const size_t warp_global = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const size_t nwarps = ((size_t)gridDim.x * blockDim.x) >> 5;
+    for (size_t op = warp_global; op < batch; op += nwarps) {
+        const uint64_t lo = off[op], hi = off[op + 1];
+        if (hi < lo) {
+            if (lane == 0) {
+                record_status(status, DOT_EINVAL);
+                cout[op] = 0;
+            }
+            continue;
+        }
+        const size_t m = (size_t)(hi - lo);
+        uint32_t cin = 0;
+        for (size_t c0 = 0; c0 < m; c0 += 32 * K) {
+            uint32_t x[K][1], y[K][1];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const size_t li = c0 + (size_t)k * 32 + lane;
+                if (li < m) {
+                    x[k][0] = ld_stream1(a + lo + li);
+                    y[k][0] = ld_stream1(b + lo + li);
+                } else {
+                    x[k][0] = y[k][0] = 0;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const size_t li = c0 + (size_t)k * 32 + lane;
+                Segment<SUB, 1> sg;
+                sg.phase12(x[k], y[k]);
+                const bool on = li < m;
+                WarpCarry wc;
+                wc.resolve(on ? sg.g() : 0u, on ? sg.p() : 0u, lane == 0 ? cin : 0u, 1u, 0x80000000u);
+                const uint32_t c = wc.carry_in(lane);
+                sg.apply(c);
+                if (on) {
+                    st_stream1(s + lo + li, sg.r[0]);
+                    if (li == m - 1) cout[op] = sg.cout(c);
+                }
+                cin = wc.carry_out(31);
+            }
+        }
+        if (m == 0 && lane == 0) cout[op] = 0;
+    }
+}
+
+// =========================================================== host launchers
+template <bool SUB, int SEG>
+static cudaError_t launch_warp(dot_ctx_t ctx, const dot_plan_t &pl, const uint32_t *a,
+                               const uint32_t *b, uint32_t *s, uint32_t *cout, size_t m,
+                               size_t batch, cudaStream_t st)
+{
+    const int lpo = pl.lanes_per_op, nch = pl.chunks;
+    const int opw = 32 / lpo;
+    const int U = (nch == 1) ? 2 : 1;
+    const size_t warp_iters = dot_ceil_div(batch, (size_t)opw * U);
+    const size_t blocks_needed = dot_ceil_div(warp_iters, WARP_KERNEL_THREADS / 32);
+    const void *fn;
+    if (nch == 1) fn = (const void *)addsub_warp_kernel<SUB, SEG, 1, 2>;
+    else if (nch == 2) fn = (const void *)addsub_warp_kernel<SUB, SEG, 2, 1>;
+    else fn = (const void *)addsub_warp_kernel<SUB, SEG, 4, 1>;
+    const size_t cap = (size_t)ctx->num_sms * dot_blocks_per_sm(fn, WARP_KERNEL_THREADS, 0);
+    const unsigned grid = (unsigned)(blocks_needed < cap ? blocks_needed : cap);
+    if (nch == 1)
+        addsub_warp_kernel<SUB, SEG, 1, 2><<<grid, WARP_KERNEL_THREADS, 0, st>>>(a, b, s, cout, m, batch, lpo, nch);
+    else if (nch == 2)
+        addsub_warp_kernel<SUB, SEG, 2, 1><<<grid, WARP_KERNEL_THREADS, 0, st>>>(a, b, s, cout, m, batch, lpo, nch);
+    else
+        addsub_warp_kernel<SUB, SEG, 4, 1><<<grid, WARP_KERNEL_THREADS, 0, st>>>(a, b, s, cout, m, batch, lpo, nch);
+    return cudaGetLastError();
+}
+
+template <bool SUB, int SEG>
+static dot_status_t launch_tile(dot_ctx_t ctx, const dot_plan_t &pl, const uint32_t *a,
+                                const uint32_t *b, uint32_t *s, uint32_t *cout, size_t m,
+                                size_t batch, cudaStream_t st)
+{
+    LookbackArgs lb;
+    const size_t tiles = (size_t)pl.tiles * batch;
+    dot_status_t rc = dot_lookback_prepare(ctx, tiles, &lb);
+    if (rc != DOT_OK) return rc;
+    ctx->debug_skip_tile = -1;   // the hook fires once
+    const void *fn;
+    if (pl.chunks == 1) fn = (const void *)addsub_tile_kernel<SUB, SEG, 1>;
+    else if (pl.chunks == 2) fn = (const void *)addsub_tile_kernel<SUB, SEG, 2>;
+    else fn = (const void *)addsub_tile_kernel<SUB, SEG, 4>;
+    const size_t cap = (size_t)ctx->num_sms * dot_blocks_per_sm(fn, DOT_TILE_THREADS, 0);
+    const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
+    const unsigned long long tpo = pl.tiles;
+    if (pl.chunks == 1)
+        addsub_tile_kernel<SUB, SEG, 1><<<grid, DOT_TILE_THREADS, 0, st>>>(a, b, s, cout, m, batch, tpo, lb);
+    else if (pl.chunks == 2)
+        addsub_tile_kernel<SUB, SEG, 2><<<grid, DOT_TILE_THREADS, 0, st>>>(a, b, s, cout, m, batch, tpo, lb);
+    else
+        addsub_tile_kernel<SUB, SEG, 4><<<grid, DOT_TILE_THREADS, 0, st>>>(a, b, s, cout, m, batch, tpo, lb);
+    return cudaGetLastError() == cudaSuccess ? DOT_OK : DOT_ECUDA;
+}
+
+template <bool SUB>
+static dot_status_t addsub_batched(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b, uint32_t *s,
+                                   uint32_t *cout, size_t m, size_t batch, cudaStream_t st)
+{
+    dot_status_t rc = dot_check_ctx(ctx);
+    if (rc != DOT_OK) return rc;
+    if (batch == 0) return DOT_OK;
+    if (!cout) return DOT_EINVAL;
+    if (m && (!a || !b || !s)) return DOT_EINVAL;
+    if (m > SIZE_MAX / 4 / batch) return DOT_EINVAL;
+    const size_t bytes = m * batch * 4;
+    if (partial_overlap(s, bytes, a, bytes) || partial_overlap(s, bytes, b, bytes)) return DOT_EINVAL;
+    if (any_overlap(cout, batch * 4, s, bytes) || any_overlap(cout, batch * 4, a, bytes) ||
+        any_overlap(cout, batch * 4, b, bytes))
+        return DOT_EINVAL;
+    if (m == 0) return cudaMemsetAsync(cout, 0, batch * 4, st) == cudaSuccess ? DOT_OK : DOT_ECUDA;
+    const bool vec = (m % 4 == 0) && aligned16(a) && aligned16(b) && aligned16(s);
+    dot_plan_t pl;
+    rc = dot_make_plan(SUB ? DOT_OP_SUB : DOT_OP_ADD, m, batch, vec, &pl);
+    if (rc != DOT_OK) return rc;
+    if (pl.kernel == DOT_K_ADDSUB_WARP) {
+        cudaError_t e = vec ? launch_warp<SUB, 4>(ctx, pl, a, b, s, cout, m, batch, st)
+                            : launch_warp<SUB, 1>(ctx, pl, a, b, s, cout, m, batch, st);
+        return e == cudaSuccess ? DOT_OK : DOT_ECUDA;
+    }
+    return vec ? launch_tile<SUB, 4>(ctx, pl, a, b, s, cout, m, batch, st)
+               : launch_tile<SUB, 1>(ctx, pl, a, b, s, cout, m, batch, st);
+}
+
+template <bool SUB>
+static dot_status_t addsub_ragged(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b, uint32_t *s,
+                                  uint32_t *cout, const uint64_t *off, size_t batch, cudaStream_t st)
+{
+    dot_status_t rc = dot_check_ctx(ctx);
+    if (rc != DOT_OK) return rc;
+    if (batch == 0) return DOT_OK;
+    if (!a || !b || !s || !cout || !off) return DOT_EINVAL;
+    const void *fn = (const void *)addsub_ragged_kernel<SUB>;
+    const size_t cap = (size_t)ctx->num_sms * dot_blocks_per_sm(fn, WARP_KERNEL_THREADS, 0);
+    const size_t need = dot_ceil_div(batch, WARP_KERNEL_THREADS / 32);
+    const unsigned grid = (unsigned)(need < cap ? need : cap);
+    addsub_ragged_kernel<SUB><<<grid, WARP_KERNEL_THREADS, 0, st>>>(a, b, s, cout, off, batch, ctx->d_status);
+    return cudaGetLastError() == cudaSuccess ? DOT_OK : DOT_ECUDA;
+}
+
+extern "C" {
+
+DOT_API dot_status_t dot_add(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b, uint32_t *s,
+                             uint32_t *carry_out, size_t m, size_t batch, dot_stream_t stream)
+{
+    return addsub_batched<false>(ctx, a, b, s, carry_out, m, batch, (cudaStream_t)stream);
+}
+
+DOT_API dot_status_t dot_sub(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b, uint32_t *d,
+                             uint32_t *borrow_out, size_t m, size_t batch, dot_stream_t stream)
+{
+    return addsub_batched<true>(ctx, a, b, d, borrow_out, m, batch, (cudaStream_t)stream);
+}
+
+DOT_API dot_status_t dot_add_ragged(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b, uint32_t *s,
+                                    uint32_t *carry_out, const uint64_t *off, size_t batch,
+                                    dot_stream_t stream)
+{
+    return addsub_ragged<false>(ctx, a, b, s, carry_out, off, batch, (cudaStream_t)stream);
+}
+
+DOT_API dot_status_t dot_sub_ragged(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b, uint32_t *d,
+                                    uint32_t *borrow_out, const uint64_t *off, size_t batch,
+                                    dot_stream_t stream)
+{
+    return addsub_ragged<true>(ctx, a, b, d, borrow_out, off, batch, (cudaStream_t)stream);
+}
+
+}  // extern "C"

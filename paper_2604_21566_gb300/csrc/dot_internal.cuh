@@ -1,0 +1,214 @@
+// dot_internal.cuh -- shared device primitives and the context layout of libdot.
+//
+// Carry handling follows DoT's addition (Alg. 1, Sec. 3.1): Phase 1 adds the
+// limbs independently, Phase 2 derives per-limb generate bits (r < a, the
+// carry lemma of the appendix) and propagate bits (r == 2^32-1), and
+// Phases 3-4 resolve the carries with the Kogge-Stone mask trick
+//     carries = ((G << 1 | c_in) + P) ^ P,
+// an integer add on bitmasks whose carry chain runs exactly through the
+// propagating positions.  The same identity is used at three levels: limbs
+// inside a thread's segment, segments across the 32 lanes of a warp (masks
+// from __ballot_sync), and tiles across thread blocks (decoupled look-back).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "dot.h"
+
+#define DOT_FULL 0xffffffffu
+
+// ------------------------------------------------------------------ context
+struct dot_ctx {
+    int device;
+    int num_sms;
+    // sticky device status (DOT_OK or an error code), cleared by dot_ctx_check
+    uint32_t *d_status;
+    // look-back scratch: [0] tile ticket, [1] blocks done, [2..3] 64-bit epoch
+    unsigned long long *d_counters;
+    // per-tile look-back states, (epoch << 2) | code
+    unsigned long long *d_tile_state;
+    size_t tile_state_cap;
+    uint64_t wait_limit_ns;
+    int64_t debug_skip_tile;
+    // staging for the host-buffer entry points
+    void *d_stage;
+    size_t stage_bytes;
+    cudaStream_t side[2];
+    cudaEvent_t ev[6];   // [0,1] kernel done per side stream, [2] start, [3,4] side ends
+};
+
+// look-back tile state codes (low two bits of a state word)
+enum { LB_EMPTY = 0, LB_PROP = 1, LB_INCL0 = 2, LB_INCL1 = 3 };
+
+struct LookbackArgs {
+    unsigned long long *state;      // one word per tile (ticket order)
+    unsigned long long *counters;   // ticket, done, epoch
+    uint32_t *status;
+    uint64_t wait_limit_ns;
+    long long skip_tile;            // debug hook: tile of op 0 that never publishes, or -1
+};
+
+// -------------------------------------------------------------- small utils
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void record_status(uint32_t *status, uint32_t code)
+{
+    if (status) atomicCAS(status, (uint32_t)DOT_OK, code);
+}
+
+// streaming loads/stores: each byte is touched once
+__device__ __forceinline__ uint4 ld_stream4(const uint32_t *p)
+{
+    return __ldcs(reinterpret_cast<const uint4 *>(p));
+}
+__device__ __forceinline__ uint32_t ld_stream1(const uint32_t *p) { return __ldcs(p); }
+__device__ __forceinline__ void st_stream4(uint32_t *p, uint4 v)
+{
+    __stcs(reinterpret_cast<uint4 *>(p), v);
+}
+__device__ __forceinline__ void st_stream1(uint32_t *p, uint32_t v) { __stcs(p, v); }
+
+// --------------------------------------------------------- segment phases
+// One thread's segment of SEG consecutive limbs.  Phase 1 forms r_i = a_i +- b_i
+// (mod 2^32) independently; Phase 2 records the generate bit g_i and the
+// propagate bit p_i of each limb in the masks gm, pm:
+//   add: g_i = [r_i < a_i],  p_i = [r_i == 2^32-1]
+//   sub: g_i = [a_i < b_i],  p_i = [a_i == b_i]   (borrows instead of carries)
+template <bool SUB, int SEG>
+struct Segment {
+    uint32_t r[SEG];
+    uint32_t gm, pm;
+
+    __device__ __forceinline__ void phase12(const uint32_t (&x)[SEG], const uint32_t (&y)[SEG])
+    {
+        gm = 0;
+        pm = 0;
+#pragma unroll
+        for (int i = 0; i < SEG; ++i) {
+            if (!SUB) {
+                r[i] = x[i] + y[i];
+                gm |= (uint32_t)(r[i] < x[i]) << i;
+                pm |= (uint32_t)(r[i] == DOT_FULL) << i;
+            } else {
+                r[i] = x[i] - y[i];
+                gm |= (uint32_t)(x[i] < y[i]) << i;
+                pm |= (uint32_t)(x[i] == y[i]) << i;
+            }
+        }
+    }
+    // segment generate: carry out of the segment with carry-in 0
+    __device__ __forceinline__ uint32_t g() const { return (((gm << 1) + pm) >> SEG) & 1u; }
+    // segment propagate: every limb propagates
+    __device__ __forceinline__ uint32_t p() const
+    {
+        return pm == (SEG == 32 ? DOT_FULL : ((1u << SEG) - 1u));
+    }
+    // Phases 3-4: add the resolved carry into each limb.  cin is the carry
+    // into limb 0; the mask trick gives the carry into every limb at once.
+    __device__ __forceinline__ void apply(uint32_t cin)
+    {
+        const uint32_t cm = (((gm << 1) | cin) + pm) ^ pm;
+#pragma unroll
+        for (int i = 0; i < SEG; ++i) {
+            const uint32_t c = (cm >> i) & 1u;
+            r[i] = SUB ? r[i] - c : r[i] + c;
+        }
+    }
+    // carry out of the segment for carry-in cin
+    __device__ __forceinline__ uint32_t cout(uint32_t cin) const
+    {
+        return ((((gm << 1) | cin) + pm) >> SEG) & 1u;
+    }
+};
+
+// ---------------------------------------------------- warp carry-lookahead
+// Lanes are grouped in runs of `lpo` consecutive lanes (runs start at the
+// bits of start_mask; top_mask marks each run's last lane).  Lane l supplies
+// its segment's (g, p); lanes of a run form one carry chain, with carry-in
+// `run_cin` taken from the run's first lane.  Returns the mask of carries
+// INTO each lane's segment (bit l).  No carry crosses from one run into the
+// next: the generate bit of a run's top lane and its propagate bit are
+// masked, and a run's carry-out is computed by run_carry_out().
+struct WarpCarry {
+    uint32_t G, P, C;
+
+    __device__ __forceinline__ void resolve(uint32_t g, uint32_t p, uint32_t run_cin,
+                                            uint32_t start_mask, uint32_t top_mask)
+    {
+        G = __ballot_sync(DOT_FULL, g);
+        P = __ballot_sync(DOT_FULL, p);
+        const uint32_t CI = __ballot_sync(DOT_FULL, run_cin) & start_mask;
+        const uint32_t X = ((G << 1) & ~start_mask) | CI;
+        const uint32_t Pm = P & ~top_mask;
+        C = (X + Pm) ^ Pm;
+    }
+    __device__ __forceinline__ uint32_t carry_in(int lane) const { return (C >> lane) & 1u; }
+    // carry out of the segment held by lane L
+    __device__ __forceinline__ uint32_t carry_out(int L) const
+    {
+        return ((G >> L) | ((P >> L) & (C >> L))) & 1u;
+    }
+};
+
+// run masks for runs of lpo lanes (lpo <= 32): start bits at 0, lpo, 2 lpo, ...
+__host__ __device__ inline uint32_t run_start_mask(int lpo)
+{
+    uint32_t m = 0;
+    for (int k = 0; k + lpo <= 32; k += lpo) m |= 1u << k;
+    return m;
+}
+__host__ __device__ inline uint32_t run_top_mask(int lpo)
+{
+    uint32_t m = 0;
+    for (int k = 0; k + lpo <= 32; k += lpo) m |= 1u << (k + lpo - 1);
+    return m;
+}
+
+// composition of carry states: segment (g_hi, p_hi) above (g_lo, p_lo)
+__device__ __forceinline__ void gp_compose(uint32_t &g, uint32_t &p, uint32_t g_hi, uint32_t p_hi)
+{
+    g = g_hi | (p_hi & g);
+    p = p_hi & p;
+}
+
+// ------------------------------------------------------------ host helpers
+dot_status_t dot_lookback_prepare(dot_ctx_t ctx, size_t tiles, LookbackArgs *out);
+dot_status_t dot_check_ctx(dot_ctx_t ctx);
+int dot_blocks_per_sm(const void *kernel, int threads, size_t smem);
+
+// ranges [p, p + n) overlap partially (not identical, not disjoint)
+static inline bool partial_overlap(const void *x, size_t xn, const void *y, size_t yn)
+{
+    const uintptr_t a = (uintptr_t)x, b = (uintptr_t)y;
+    if (!xn || !yn) return false;
+    if (a == b) return false;
+    return a < b + yn && b < a + xn;
+}
+static inline bool any_overlap(const void *x, size_t xn, const void *y, size_t yn)
+{
+    const uintptr_t a = (uintptr_t)x, b = (uintptr_t)y;
+    if (!xn || !yn) return false;
+    return a < b + yn && b < a + xn;
+}
+__host__ __device__ inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }

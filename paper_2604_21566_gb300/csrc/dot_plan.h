@@ -1,0 +1,80 @@
+// dot_plan.h -- host-side choice of kernel and shape for one batched call.
+// Pure integer logic (no CUDA calls), shared by the launchers and the
+// exported dot_plan_batched().
+#pragma once
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "dot.h"
+
+enum {
+    DOT_K_NONE = 0,
+    DOT_K_ADDSUB_WARP = 1,   // whole ops inside one warp (runs of lanes)
+    DOT_K_ADDSUB_TILE = 2,   // tiles of 256 threads chained by look-back
+    DOT_K_MUL_COLSUM = 3     // column-block sums + carry resolution
+};
+
+#define DOT_TILE_THREADS 256
+#define DOT_WARP_MAX_CHUNKS 4
+
+static inline size_t dot_ceil_div(size_t a, size_t b) { return (a + b - 1) / b; }
+
+// Columns per thread block of the multiply for operand length m.
+static inline int dot_mul_cols(size_t m)
+{
+    return m <= 16 ? 4 : (m <= 256 ? 8 : 16);
+}
+
+static inline dot_status_t dot_make_plan(int op, size_t m, size_t batch, bool vec, dot_plan_t *pl)
+{
+    pl->kernel = DOT_K_NONE;
+    pl->seg_limbs = 1;
+    pl->lanes_per_op = 0;
+    pl->chunks = 0;
+    pl->tile_limbs = 0;
+    pl->tiles = 0;
+    pl->m_pad = m;
+    if (op != DOT_OP_ADD && op != DOT_OP_SUB && op != DOT_OP_MUL) return DOT_EINVAL;
+    if (batch == 0) return DOT_OK;
+    if (op == DOT_OP_MUL) {
+        if (m == 0) return DOT_OK;
+        if (m > DOT_MUL_MAX_LIMBS) return DOT_EUNSUPPORTED;
+        const int R = dot_mul_cols(m);
+        pl->kernel = DOT_K_MUL_COLSUM;
+        pl->seg_limbs = R;
+        pl->m_pad = dot_ceil_div(m, (size_t)R) * R;
+        pl->lanes_per_op = (int)(pl->m_pad / R);
+        pl->chunks = 2;
+        return DOT_OK;
+    }
+    if (m == 0) {
+        // carries are 0; the warp kernel writes them
+        pl->kernel = DOT_K_ADDSUB_WARP;
+        pl->lanes_per_op = 1;
+        pl->chunks = 1;
+        return DOT_OK;
+    }
+    const int seg = vec ? 4 : 1;
+    const size_t q = dot_ceil_div(m, (size_t)seg);   // segments per op
+    pl->seg_limbs = seg;
+    if (q <= 32u * DOT_WARP_MAX_CHUNKS) {
+        pl->kernel = DOT_K_ADDSUB_WARP;
+        if (q <= 32) {
+            pl->lanes_per_op = (int)q;
+            pl->chunks = 1;
+        } else {
+            pl->lanes_per_op = 32;
+            pl->chunks = (int)dot_ceil_div(q, 32);
+        }
+        return DOT_OK;
+    }
+    pl->kernel = DOT_K_ADDSUB_TILE;
+    pl->lanes_per_op = DOT_TILE_THREADS;
+    // segments per thread: 4 for long operands, fewer for short ones
+    const size_t per4 = (size_t)DOT_TILE_THREADS * seg * 4;
+    pl->chunks = m >= per4 ? 4 : (m >= per4 / 2 ? 2 : 1);
+    pl->tile_limbs = (uint64_t)DOT_TILE_THREADS * seg * pl->chunks;
+    pl->tiles = dot_ceil_div(m, (size_t)pl->tile_limbs);
+    return DOT_OK;
+}

@@ -1,0 +1,66 @@
+"""The C-ABI library builds, loads and exports every symbol include/dot.h
+declares; host-side logic (argument checks, launch plans) needs no GPU."""
+import ctypes
+
+import pytest
+
+from paper_2604_21566_gb300 import build as B
+from paper_2604_21566_gb300 import dot
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return dot.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    names = dot.header_functions()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    # and the binding declares a signature for each of them
+    assert set(names) <= set(dot._SIGS), set(names) - set(dot._SIGS)
+
+
+def test_status_strings_and_version(L):
+    assert L.dot_abi_version() == 1
+    for code in range(6):
+        assert L.dot_status_str(code)
+    assert L.dot_status_str(99) == b"unknown status"
+
+
+def test_null_context_rejected_without_gpu(L):
+    v = ctypes.c_void_p
+    assert L.dot_add(None, v(0), v(0), v(0), v(0), 4, 4, None) == dot.EINVAL
+    assert L.dot_mul(None, v(0), v(0), v(0), 4, 4, None) == dot.EINVAL
+    assert L.dot_ctx_create(None, 0) == dot.EINVAL
+    assert L.dot_ctx_set_wait_limit(None, 5) == dot.EINVAL
+    L.dot_ctx_destroy(None)
+
+
+def test_plans():
+    # whole ops inside a warp
+    p = dot.plan(dot.OP_ADD, 128, 1 << 20)
+    assert (p.kernel, p.seg_limbs, p.lanes_per_op, p.chunks) == (1, 4, 32, 1)
+    p = dot.plan(dot.OP_ADD, 32, 4096)
+    assert (p.kernel, p.lanes_per_op, p.chunks) == (1, 8, 1)
+    p = dot.plan(dot.OP_SUB, 512, 10)
+    assert (p.kernel, p.lanes_per_op, p.chunks) == (1, 32, 4)
+    p = dot.plan(dot.OP_ADD, 7, 10, vector_ok=False)
+    assert (p.kernel, p.seg_limbs, p.lanes_per_op) == (1, 1, 7)
+    # long operands: tiles chained by look-back
+    p = dot.plan(dot.OP_ADD, 1 << 17, 64)
+    assert p.kernel == 2 and p.tile_limbs == 4096 and p.tiles == 32
+    p = dot.plan(dot.OP_ADD, 513, 3)
+    assert p.kernel == 2 and p.tiles == 1
+    # multiply: two column blocks per lane, R columns each
+    for m, R, T in ((8, 4, 2), (32, 8, 4), (128, 8, 16), (256, 8, 32), (512, 16, 32), (100, 8, 13)):
+        p = dot.plan(dot.OP_MUL, m, 1)
+        assert (p.kernel, p.seg_limbs, p.lanes_per_op) == (3, R, T), m
+        assert p.m_pad == R * T
+    with pytest.raises(dot.DotError):
+        dot.plan(dot.OP_MUL, 513, 1)
+    with pytest.raises(dot.DotError):
+        dot.plan(7, 4, 1)
+    assert dot.plan(dot.OP_ADD, 4, 0).kernel == 0
