@@ -385,8 +385,32 @@ def reference_arm(args, rank, world):
     }), flush=True)
 
 
+def profile_case(args):
+    """Small case for ncu: dot_add on 2^18 pairs of 4096-bit operands
+    (403 MB of algorithmic traffic, larger than L2), a few launches."""
+    import torch
+    from paper_2604_21566_gb300 import dot
+    from paper_2604_21566_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    d = W.addsub_bandwidth(short_batch=1 << 18, long_batch=0)
+    x, y = d["add_short"]
+    a = torch.from_numpy(x.view(np.int32)).cuda()
+    b = torch.from_numpy(y.view(np.int32)).cuda()
+    s = torch.empty_like(a)
+    c = torch.empty(a.shape[0], dtype=torch.int32, device="cuda")
+    ctx = dot.Context(0)
+    for _ in range(args.launches):
+        dot.add(a, b, out=s, carry=c, ctx=ctx)
+    torch.cuda.synchronize()
+    assert ctx.check() == dot.OK
+    print("profile case done")
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run only the small ncu case of the dominant kernel")
+    ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
@@ -397,6 +421,11 @@ def main():
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     rank, world, local = dist_info()
+    if args.profile_case:
+        from paper_2604_21566_gb300 import build as B
+        B.build()
+        profile_case(args)
+        return
     if args.impl == "reference":
         reference_arm(args, rank, world)
         return
