@@ -15,32 +15,9 @@
 // Subtraction is the same with borrows (Sec. 3.1, "Subtraction").
 #include "dot_internal.cuh"
 #include "dot_plan.h"
+#include "dot_addsub.cuh"
 
 #define WARP_KERNEL_THREADS 256
-
-// --------------------------------------------------------------- loading
-template <int SEG>
-__device__ __forceinline__ void load_seg(const uint32_t *p, uint32_t (&v)[SEG])
-{
-    if constexpr (SEG == 4) {
-        const uint4 q = ld_stream4(p);
-        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-    } else {
-#pragma unroll
-        for (int i = 0; i < SEG; ++i) v[i] = ld_stream1(p + i);
-    }
-}
-
-template <int SEG>
-__device__ __forceinline__ void store_seg(uint32_t *p, const uint32_t (&v)[SEG])
-{
-    if constexpr (SEG == 4) {
-        st_stream4(p, make_uint4(v[0], v[1], v[2], v[3]));
-    } else {
-#pragma unroll
-        for (int i = 0; i < SEG; ++i) st_stream1(p + i, v[i]);
-    }
-}
 
 // ======================================================= warp kernel (1)
 // Each op lies inside one warp: runs of `lpo` lanes per op (several ops per
@@ -268,60 +245,23 @@ addsub_tile_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint32_t *
 }
 
 // ===================================================== ragged kernel (one warp per op)
-// Op k has off[k+1] - off[k] limbs.  The warp walks its op in groups of
-// 4 x 32 limbs (loads first), resolving each 32-limb chunk with the ballot
-// lookahead and passing the chunk carry-out on -- Alg. 1's chunk loop with
-// w = 32 lanes.
 template <bool SUB>
 __global__ void __launch_bounds__(WARP_KERNEL_THREADS)
 addsub_ragged_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint32_t *cout,
                      const uint64_t *off, size_t batch, uint32_t *status)
 {
-    constexpr int K = 4;
-    const int lane = (int)lane_id();
     const size_t warp_global = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const size_t nwarps = ((size_t)gridDim.x * blockDim.x) >> 5;
     for (size_t op = warp_global; op < batch; op += nwarps) {
         const uint64_t lo = off[op], hi = off[op + 1];
         if (hi < lo) {
-            if (lane == 0) {
+            if (lane_id() == 0) {
                 record_status(status, DOT_EINVAL);
                 cout[op] = 0;
             }
             continue;
         }
-        const size_t m = (size_t)(hi - lo);
-        uint32_t cin = 0;
-        for (size_t c0 = 0; c0 < m; c0 += 32 * K) {
-            uint32_t x[K][1], y[K][1];
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const size_t li = c0 + (size_t)k * 32 + lane;
-                if (li < m) {
-                    x[k][0] = ld_stream1(a + lo + li);
-                    y[k][0] = ld_stream1(b + lo + li);
-                } else {
-                    x[k][0] = y[k][0] = 0;
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const size_t li = c0 + (size_t)k * 32 + lane;
-                Segment<SUB, 1> sg;
-                sg.phase12(x[k], y[k]);
-                const bool on = li < m;
-                WarpCarry wc;
-                wc.resolve(on ? sg.g() : 0u, on ? sg.p() : 0u, lane == 0 ? cin : 0u, 1u, 0x80000000u);
-                const uint32_t c = wc.carry_in(lane);
-                sg.apply(c);
-                if (on) {
-                    st_stream1(s + lo + li, sg.r[0]);
-                    if (li == m - 1) cout[op] = sg.cout(c);
-                }
-                cin = wc.carry_out(31);
-            }
-        }
-        if (m == 0 && lane == 0) cout[op] = 0;
+        addsub_warp_op<SUB>(a + lo, b + lo, s + lo, (size_t)(hi - lo), cout + op);
     }
 }
 

@@ -94,6 +94,7 @@ DOT_API void dot_ctx_destroy(dot_ctx_t c)
     if (!c) return;
     set_device(c->device);
     cudaDeviceSynchronize();
+    dot_mixed_release(c);
     for (int i = 0; i < 6; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     for (int i = 0; i < 2; ++i)

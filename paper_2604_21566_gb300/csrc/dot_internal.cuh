@@ -37,7 +37,11 @@ struct dot_ctx {
     size_t stage_bytes;
     cudaStream_t side[2];
     cudaEvent_t ev[6];   // [0,1] kernel done per side stream, [2] start, [3,4] side ends
+    // mixed-batch scratch and captured graph (dot_mixed.cu), created on first use
+    void *mixed;
 };
+
+void dot_mixed_release(dot_ctx_t ctx);
 
 // look-back tile state codes (low two bits of a state word)
 enum { LB_EMPTY = 0, LB_PROP = 1, LB_INCL0 = 2, LB_INCL1 = 3 };

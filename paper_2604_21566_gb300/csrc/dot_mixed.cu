@@ -1,6 +1,331 @@
 // dot_mixed.cu -- mixed ragged batches of add / sub / mul descriptors.
+//
+// The paper runs one operation at a time on one core.  Here a batch of many
+// operations of uneven sizes goes through one pass on the device:
+//   1. classify: each descriptor gets a size bucket (by op and limb count);
+//      per-block histograms, one atomic per bucket per block for its slot;
+//   2. plan: one warp turns the bucket counts into offsets and work-item
+//      ranges (and clears the counts for the next call);
+//   3. scatter: op indices are written bucket by bucket;
+//   4. run: one persistent kernel; each warp takes work items from a global
+//      counter, heaviest buckets first (longest-processing-time order), and
+//      runs the multiply (column-block sums, Alg. 2) or add/sub (Alg. 1) code
+//      for the item's ops.  Small multiplies share a warp: a bucket fixes the
+//      run width T, and each op of the item takes a run of T lanes.
+// The four launches are captured once into a CUDA graph per context; later
+// calls only update the graph's kernel-node parameters and replay it.
+#include <stdlib.h>
+#include <string.h>
+
 #include "dot_internal.cuh"
 #include "dot_plan.h"
+#include "dot_addsub.cuh"
+#include "dot_mul.cuh"
+
+// bucket ids, in processing order
+enum { BK_M16 = 0, BK_M8C, BK_M8B, BK_M8A, BK_M4, BK_ASL, BK_ASS, NBK };
+#define MIX_WARPS 4
+#define MIX_REGION_WORDS 1056   // largest per-warp staging: 2 * 512 + 2 * 16 words
+#define MIX_MAX_OPS (1ull << 28)
+
+struct MixedMeta {
+    uint32_t count[NBK];   // filled by classify, cleared by plan
+    uint32_t n[NBK];       // ops per bucket
+    uint32_t base[NBK];    // first slot of each bucket in `order`
+    uint32_t item_base[NBK + 1];
+    uint32_t pad;
+    unsigned long long next_item;
+    unsigned long long done;
+};
+
+struct MixedScratch {
+    uint32_t *slot;
+    uint32_t *order;
+    MixedMeta *meta;
+    size_t cap;
+    cudaGraphExec_t exec;
+    cudaGraph_t graph;
+    cudaGraphNode_t node[4];
+    int persist_blocks;
+};
+
+__host__ __device__ inline int bucket_ops_per_item(int bk)
+{
+    switch (bk) {
+    case BK_M8B: return 2;
+    case BK_M8A: return 4;
+    case BK_M4: return 8;
+    default: return 1;
+    }
+}
+
+// bucket of one descriptor; -1: nothing to run (m == 0), -2: bad op, -3: mul too long
+__device__ __forceinline__ int bucket_of(uint32_t op, uint32_t m)
+{
+    if (op > DOT_OP_MUL) return -2;
+    if (m == 0) return -1;
+    if (op != DOT_OP_MUL) return m > 128 ? BK_ASL : BK_ASS;
+    if (m > DOT_MUL_MAX_LIMBS) return -3;
+    if (m > 256) return BK_M16;
+    if (m > 128) return BK_M8C;
+    if (m > 64) return BK_M8B;
+    if (m > 16) return BK_M8A;
+    return BK_M4;
+}
+
+__global__ void __launch_bounds__(256)
+mixed_classify(const dot_desc_t *desc, size_t nops, uint32_t *slot, MixedMeta *meta, uint32_t *carry,
+               uint32_t *status)
+{
+    __shared__ uint32_t s_cnt[NBK], s_base[NBK];
+    if (threadIdx.x < NBK) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int bk = -1;
+    uint32_t rank = 0;
+    if (i < nops) {
+        const uint32_t op = desc[i].op, m = desc[i].m;
+        bk = bucket_of(op, m);
+        if (bk < 0) {
+            carry[i] = 0;
+            if (bk == -2) record_status(status, DOT_EINVAL);
+            if (bk == -3) record_status(status, DOT_EUNSUPPORTED);
+        } else {
+            rank = atomicAdd(&s_cnt[bk], 1u);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < NBK)
+        s_base[threadIdx.x] = s_cnt[threadIdx.x] ? atomicAdd(&meta->count[threadIdx.x], s_cnt[threadIdx.x]) : 0u;
+    __syncthreads();
+    if (i < nops) slot[i] = bk >= 0 ? (((uint32_t)bk << 28) | (s_base[bk] + rank)) : 0xffffffffu;
+}
+
+__global__ void mixed_plan(MixedMeta *meta)
+{
+    if (threadIdx.x == 0) {
+        uint32_t base = 0, items = 0;
+        for (int b = 0; b < NBK; ++b) {
+            const uint32_t c = meta->count[b];
+            meta->n[b] = c;
+            meta->base[b] = base;
+            meta->item_base[b] = items;
+            base += c;
+            items += (c + bucket_ops_per_item(b) - 1) / bucket_ops_per_item(b);
+            meta->count[b] = 0;
+        }
+        meta->item_base[NBK] = items;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+mixed_scatter(const uint32_t *slot, size_t nops, const MixedMeta *meta, uint32_t *order)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nops) return;
+    const uint32_t s = slot[i];
+    if (s == 0xffffffffu) return;
+    order[meta->base[s >> 28] + (s & 0x0fffffffu)] = (uint32_t)i;
+}
+
+// the ops of one multiply work item: run grp of the warp takes op k0 + grp
+template <int R, int T>
+__device__ __forceinline__ void mixed_mul_item(const dot_desc_t *desc, const uint32_t *order, uint32_t base,
+                                               uint32_t n, uint32_t k0, const uint32_t *a, const uint32_t *b,
+                                               uint32_t *r, uint32_t *carry, uint32_t *wsmem)
+{
+    constexpr int OPI = 32 / T;
+    constexpr int REGION = 2 * T * R + 2 * R;
+    static_assert(OPI * REGION <= MIX_REGION_WORDS, "staging region");
+    const int lane = (int)lane_id();
+    const int grp = lane / T, t = lane - grp * T;
+    const uint32_t idx = k0 + grp;
+    const bool valid = idx < n;
+    uint32_t op = 0, m = 0;
+    uint64_t ao = 0, bo = 0, ro = 0;
+    if (valid) {
+        op = order[base + idx];
+        const dot_desc_t d = desc[op];
+        m = d.m;
+        ao = d.a_off;
+        bo = d.b_off;
+        ro = d.r_off;
+    }
+    const int tn = (int)((m + R - 1) / R);
+    const int mp = tn * R;
+    uint32_t *As = wsmem + grp * REGION;
+    uint32_t *Bs = As + mp;
+    if (valid) {
+        const bool va = ((ao & 3) == 0) && aligned16(a);
+        const bool vb = ((bo & 3) == 0) && aligned16(b);
+        if (t < tn) {
+            stage_row<R>(a + ao, As, t, (int)m, va);
+            stage_row<R>(b + bo, Bs + R, t, (int)m, vb);
+        }
+        for (int k = t; k < R; k += T) {
+            Bs[k] = 0;
+            Bs[R + mp + k] = 0;
+        }
+    }
+    __syncwarp();
+    const bool vec_out = ((ro & 3) == 0) && aligned16(r);
+    mul_group<R>(As, Bs, t, T, tn, grp, valid, (int)m, mp, r + ro, vec_out, run_start_mask(T),
+                 run_top_mask(T));
+    if (valid && t == 0) carry[op] = 0;
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(MIX_WARPS * 32)
+mixed_run(const dot_desc_t *desc, const uint32_t *order, MixedMeta *meta, const uint32_t *a,
+          const uint32_t *b, uint32_t *r, uint32_t *carry)
+{
+    __shared__ __align__(16) uint32_t smem[MIX_WARPS * MIX_REGION_WORDS];
+    const int lane = (int)lane_id(), warp = (int)(threadIdx.x >> 5);
+    uint32_t *wsmem = smem + warp * MIX_REGION_WORDS;
+    const uint32_t total = meta->item_base[NBK];
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(&meta->next_item, 1ull);
+        item = __shfl_sync(DOT_FULL, item, 0);
+        if (item >= total) break;
+        int bk = 0;
+#pragma unroll
+        for (int q = 1; q < NBK; ++q)
+            if (item >= meta->item_base[q]) bk = q;
+        const uint32_t n = meta->n[bk], base = meta->base[bk];
+        const uint32_t k0 = (uint32_t)(item - meta->item_base[bk]) * bucket_ops_per_item(bk);
+        switch (bk) {
+        case BK_M16: mixed_mul_item<16, 32>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
+        case BK_M8C: mixed_mul_item<8, 32>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
+        case BK_M8B: mixed_mul_item<8, 16>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
+        case BK_M8A: mixed_mul_item<8, 8>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
+        case BK_M4: mixed_mul_item<4, 4>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
+        default: {
+            const uint32_t op = order[base + k0];
+            const dot_desc_t d = desc[op];
+            if (d.op == DOT_OP_SUB)
+                addsub_warp_op<true>(a + d.a_off, b + d.b_off, r + d.r_off, d.m, carry + op);
+            else
+                addsub_warp_op<false>(a + d.a_off, b + d.b_off, r + d.r_off, d.m, carry + op);
+        }
+        }
+    }
+    // the last warp out clears the work counter for the next call
+    if (lane == 0) {
+        __threadfence();
+        const unsigned long long prev = atomicAdd(&meta->done, 1ull);
+        if (prev == (unsigned long long)gridDim.x * MIX_WARPS - 1) {
+            meta->next_item = 0;
+            meta->done = 0;
+            __threadfence();
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host
+static MixedScratch *g_scratch_of(dot_ctx_t ctx);
+
+struct MixedArgs {
+    const dot_desc_t *desc;
+    size_t nops;
+    uint32_t *slot, *order, *carry, *status, *r;
+    MixedMeta *meta;
+    const uint32_t *a, *b;
+};
+
+static void fill_params(const MixedArgs &A, void **p0, void **p1, void **p2, void **p3)
+{
+    // pointers to the argument values of the four kernels (must outlive the call)
+    p0[0] = (void *)&A.desc; p0[1] = (void *)&A.nops; p0[2] = (void *)&A.slot; p0[3] = (void *)&A.meta;
+    p0[4] = (void *)&A.carry; p0[5] = (void *)&A.status;
+    p1[0] = (void *)&A.meta;
+    p2[0] = (void *)&A.slot; p2[1] = (void *)&A.nops; p2[2] = (void *)&A.meta; p2[3] = (void *)&A.order;
+    p3[0] = (void *)&A.desc; p3[1] = (void *)&A.order; p3[2] = (void *)&A.meta; p3[3] = (void *)&A.a;
+    p3[4] = (void *)&A.b; p3[5] = (void *)&A.r; p3[6] = (void *)&A.carry;
+}
+
+static dot_status_t mixed_prepare(dot_ctx_t ctx, MixedScratch *S, size_t nops)
+{
+    if (S->meta == nullptr) {
+        if (cudaMalloc((void **)&S->meta, sizeof(MixedMeta)) != cudaSuccess) return DOT_ENOMEM;
+        if (cudaMemset(S->meta, 0, sizeof(MixedMeta)) != cudaSuccess) return DOT_ECUDA;
+        S->persist_blocks = ctx->num_sms * dot_blocks_per_sm((const void *)mixed_run, MIX_WARPS * 32, 0);
+    }
+    if (nops > S->cap) {
+        size_t cap = S->cap ? S->cap : 4096;
+        while (cap < nops) cap *= 2;
+        if (cudaDeviceSynchronize() != cudaSuccess) return DOT_ECUDA;
+        cudaFree(S->slot);
+        cudaFree(S->order);
+        S->slot = S->order = nullptr;
+        S->cap = 0;
+        if (cudaMalloc((void **)&S->slot, cap * 4) != cudaSuccess ||
+            cudaMalloc((void **)&S->order, cap * 4) != cudaSuccess)
+            return DOT_ENOMEM;
+        S->cap = cap;
+    }
+    return DOT_OK;
+}
+
+static dot_status_t mixed_capture(dot_ctx_t ctx, MixedScratch *S, const MixedArgs &A)
+{
+    // record the four launches once on a private stream, then keep the graph
+    cudaStream_t cs = ctx->side[0];
+    if (cudaStreamSynchronize(cs) != cudaSuccess) return DOT_ECUDA;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return DOT_ECUDA;
+    const unsigned g1 = (unsigned)((A.nops + 255) / 256);
+    mixed_classify<<<g1, 256, 0, cs>>>(A.desc, A.nops, A.slot, A.meta, A.carry, A.status);
+    mixed_plan<<<1, 32, 0, cs>>>(A.meta);
+    mixed_scatter<<<g1, 256, 0, cs>>>(A.slot, A.nops, A.meta, A.order);
+    mixed_run<<<S->persist_blocks, MIX_WARPS * 32, 0, cs>>>(A.desc, A.order, A.meta, A.a, A.b, A.r, A.carry);
+    cudaGraph_t g = nullptr;
+    if (cudaStreamEndCapture(cs, &g) != cudaSuccess || !g) return DOT_ECUDA;
+    size_t nn = 0;
+    cudaGraphNode_t nodes[8];
+    if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess || nn != 4) {
+        cudaGraphDestroy(g);
+        return DOT_ECUDA;
+    }
+    cudaGraphGetNodes(g, nodes, &nn);
+    const void *fns[4] = {(const void *)mixed_classify, (const void *)mixed_plan,
+                          (const void *)mixed_scatter, (const void *)mixed_run};
+    for (size_t i = 0; i < nn; ++i) {
+        cudaKernelNodeParams kp;
+        if (cudaGraphKernelNodeGetParams(nodes[i], &kp) != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return DOT_ECUDA;
+        }
+        for (int k = 0; k < 4; ++k)
+            if (kp.func == fns[k]) S->node[k] = nodes[i];
+    }
+    cudaGraphExec_t ex = nullptr;
+    if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return DOT_ECUDA;
+    }
+    S->graph = g;
+    S->exec = ex;
+    return DOT_OK;
+}
+
+static MixedScratch *g_scratch_of(dot_ctx_t ctx)
+{
+    if (!ctx->mixed) ctx->mixed = calloc(1, sizeof(MixedScratch));
+    return (MixedScratch *)ctx->mixed;
+}
+
+void dot_mixed_release(dot_ctx_t ctx)
+{
+    MixedScratch *S = (MixedScratch *)ctx->mixed;
+    if (!S) return;
+    if (S->exec) cudaGraphExecDestroy(S->exec);
+    if (S->graph) cudaGraphDestroy(S->graph);
+    cudaFree(S->slot);
+    cudaFree(S->order);
+    cudaFree(S->meta);
+    free(S);
+    ctx->mixed = nullptr;
+}
 
 extern "C" {
 
@@ -8,11 +333,39 @@ DOT_API dot_status_t dot_mixed_ragged(dot_ctx_t ctx, const dot_desc_t *desc, siz
                                       const uint32_t *a, const uint32_t *b, uint32_t *r,
                                       uint32_t *carry, dot_stream_t stream)
 {
-    (void)desc; (void)a; (void)b; (void)r; (void)carry; (void)stream;
     dot_status_t rc = dot_check_ctx(ctx);
     if (rc != DOT_OK) return rc;
     if (nops == 0) return DOT_OK;
-    return DOT_EUNSUPPORTED;
+    if (!desc || !a || !b || !r || !carry || nops >= MIX_MAX_OPS) return DOT_EINVAL;
+    MixedScratch *S = g_scratch_of(ctx);
+    if (!S) return DOT_ENOMEM;
+    rc = mixed_prepare(ctx, S, nops);
+    if (rc != DOT_OK) return rc;
+    MixedArgs A{desc, nops, S->slot, S->order, carry, ctx->d_status, r, S->meta, a, b};
+    if (!S->exec) {
+        rc = mixed_capture(ctx, S, A);
+        if (rc != DOT_OK) return rc;
+    }
+    void *p0[6], *p1[1], *p2[4], *p3[7];
+    fill_params(A, p0, p1, p2, p3);
+    const unsigned g1 = (unsigned)((nops + 255) / 256);
+    const void *fns[4] = {(const void *)mixed_classify, (const void *)mixed_plan,
+                          (const void *)mixed_scatter, (const void *)mixed_run};
+    void **params[4] = {p0, p1, p2, p3};
+    const dim3 grids[4] = {dim3(g1), dim3(1), dim3(g1), dim3((unsigned)S->persist_blocks)};
+    const dim3 blocks[4] = {dim3(256), dim3(32), dim3(256), dim3(MIX_WARPS * 32)};
+    for (int k = 0; k < 4; ++k) {
+        cudaKernelNodeParams kp;
+        memset(&kp, 0, sizeof kp);
+        kp.func = (void *)fns[k];
+        kp.gridDim = grids[k];
+        kp.blockDim = blocks[k];
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = params[k];
+        kp.extra = nullptr;
+        if (cudaGraphExecKernelNodeSetParams(S->exec, S->node[k], &kp) != cudaSuccess) return DOT_ECUDA;
+    }
+    return cudaGraphLaunch(S->exec, (cudaStream_t)stream) == cudaSuccess ? DOT_OK : DOT_ECUDA;
 }
 
 }  // extern "C"

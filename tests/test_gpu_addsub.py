@@ -119,7 +119,7 @@ def test_in_place_and_guard_bands(D, op):
         cbuf = torch.full((5 + 2 * G,), 0x3C3C3C3C, dtype=torch.int32, device="cuda")
         out = buf[G:G + 5 * m].view(5, m)
         cout = cbuf[G:G + 5]
-        fn(dev(x), dev(y), out=out, carry=cout)
+        fn(dev(x), dev(y), out, cout)
         torch.cuda.synchronize()
         hb, hc = host(buf), host(cbuf)
         assert (hb[:G] == 0x5A5A5A5A).all() and (hb[G + 5 * m:] == 0x5A5A5A5A).all()
