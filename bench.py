@@ -55,6 +55,25 @@ def dist_info():
     return rank, world, local
 
 
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The slowest rank's time (replicas report the whole job's throughput
+    against it); a barrier follows so no rank races ahead."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, ms: float) -> float:
+    """Whole-job rate in units per second x 1e-9: every rank processes the
+    same units (weak scaling), timed by the slowest rank."""
+    return world * units_per_rank / (ms * 1e-3) / 1e9
+
+
 def algorithmic_bytes(m: int, batch: int) -> int:
     """Operands read once (8m bytes), result written once (4m) plus the
     4-byte carry, per op."""
@@ -209,11 +228,7 @@ def gpu_arm(args, rank, world, local):
     st = ctx.check(stream)
     if st != dot.OK:
         raise RuntimeError(f"device status {st} after the timed region")
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-        torch.distributed.barrier()
+    ms = max_over_ranks(ms, world, dev)
 
     per_launch = {k: sum(e0.elapsed_time(e1) for e0, e1 in v) / len(v) for k, v in ev.items()}
     ops_step = sum(p[1].shape[0] for p in parts)
@@ -270,10 +285,7 @@ def gpu_arm(args, rank, world, local):
         ws, wc = oracle.add(x[:512], y[:512])
         exact &= bool(np.array_equal(so.numpy().view(np.uint32)[:512], ws))
     clocks = sampler.stop()
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
 
     if rank == 0:
         hbm, src = peaks()
@@ -293,7 +305,7 @@ def gpu_arm(args, rank, world, local):
             }
         cpu = cpu_baseline(data, args.cpu_seconds) if not args.no_cpu else None
         ms_step = ms / args.steps
-        value = world * ops_step / (ms_step * 1e-3) / 1e9
+        value = job_throughput(ops_step, world, ms_step)
         out = {
             "metric": METRIC, "value": round(value, 4), "unit": "Gop/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
@@ -310,7 +322,7 @@ def gpu_arm(args, rank, world, local):
                          "traffic": read_traffic(), "algorithmic_bytes_per_launch": alg},
             "parts": parts_out,
             "cpu_baseline": cpu,
-            "e2e": {"value": round(world * ops_step / (e2e_ms * 1e-3) / 1e9, 4), "unit": "Gop/s",
+            "e2e": {"value": round(job_throughput(ops_step, world, e2e_ms), 4), "unit": "Gop/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": round(e2e_ms, 4), "api": "dot_add_host / dot_sub_host"},
             "gpu_launches": 4 * args.steps,
@@ -406,8 +418,165 @@ def profile_case(args):
     print("profile case done")
 
 
+IMAD_PER_SM_CLK = 64   # 32-bit integer multiply-add lanes per SM per clock (FMA pipe)
+
+
+def int_peak():
+    """Nominal 32-bit IMAD rate (ops/s): SMs x 64 lanes x max SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    try:
+        mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
+    except Exception:
+        mhz = 2070.0
+    return sms * IMAD_PER_SM_CLK * mhz * 1e6, sms, mhz
+
+
+def _event_ms(fn, reps, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def suite(args):
+    """One JSON line per workload row: correctness mix, batched multiply per
+    size, mixed ragged batch vs one launch per size, shared-operand multiply."""
+    import torch
+    import oracle
+    from paper_2604_21566_gb300 import dot
+    from paper_2604_21566_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = dot.Context(0)
+    peak, sms, mhz = int_peak()
+
+    def dv(x):
+        return torch.from_numpy(np.ascontiguousarray(x).view(
+            np.int32 if x.dtype == np.uint32 else np.int64)).cuda()
+
+    def hs(t):
+        return t.cpu().numpy().view(np.uint32)
+
+    def emit(d):
+        d["suite"] = True
+        print(json.dumps(d), flush=True)
+
+    # -- correctness mix: 4096 x 1024-bit, latency-bound
+    d = W.correctness_mix()
+    a, b = dv(d["x"]), dv(d["y"])
+    asub, bsub = dv(d["a_sub"]), dv(d["b_sub"])
+    s = torch.empty_like(a)
+    c = torch.empty(a.shape[0], dtype=torch.int32, device="cuda")
+    p = torch.empty((a.shape[0], 64), dtype=torch.int32, device="cuda")
+    t_add = _event_ms(lambda: dot.add(a, b, s, c, ctx=ctx), 200, stream)
+    ok = np.array_equal(hs(s), oracle.add(d["x"], d["y"])[0])
+    t_sub = _event_ms(lambda: dot.sub(asub, bsub, s, c, ctx=ctx), 200, stream)
+    ok &= np.array_equal(hs(s), oracle.sub(d["a_sub"], d["b_sub"])[0])
+    t_mul = _event_ms(lambda: dot.mul(a, b, p, ctx=ctx), 200, stream)
+    ok &= np.array_equal(hs(p), oracle.mul(d["x"], d["y"], threads=oracle.cores()))
+    emit({"workload": "correctness mix: 4096 x 1024-bit (m=32), add/sub/mul", "bit_exact": bool(ok),
+          "us_per_call": {"add": round(t_add * 1e3, 2), "sub": round(t_sub * 1e3, 2),
+                          "mul": round(t_mul * 1e3, 2)},
+          "gop_s": {"add": round(4096 / t_add / 1e6, 3), "sub": round(4096 / t_sub / 1e6, 3),
+                    "mul": round(4096 / t_mul / 1e6, 3)}})
+
+    # -- batched multiply at fixed size
+    rows = []
+    for m in W.BATCHED_MUL_SIZES:
+        x, y, _ = W.batched_mul(m)
+        a, b = dv(x), dv(y)
+        p = torch.empty((x.shape[0], 2 * m), dtype=torch.int32, device="cuda")
+        ms = _event_ms(lambda: dot.mul(a, b, p, ctx=ctx), 20, stream)
+        sel = np.random.default_rng(m).integers(0, x.shape[0], 512)
+        ok = np.array_equal(hs(p)[sel], oracle.mul(x[sel], y[sel]))
+        prods = x.shape[0] * m * m
+        imad = 2.0 * prods / (ms * 1e-3)
+        rows.append({"m_limbs": m, "bits": 32 * m, "ops": x.shape[0], "ms": round(ms, 4),
+                     "gop_s": round(x.shape[0] / (ms * 1e-3) / 1e9, 4),
+                     "tera_limb_products_s": round(prods / (ms * 1e-3) / 1e12, 3),
+                     "GB_s": round(16 * m * x.shape[0] / (ms * 1e-3) / 1e9, 1),
+                     "roofline": {"bound": "alu", "achieved_imad_per_s": imad, "peak": peak,
+                                  "frac": round(imad / peak, 4)},
+                     "bit_exact_sample": bool(ok)})
+    emit({"workload": "batched multiply: 2^16 pairs at 256/1024/4096/8192 bits",
+          "int_peak": {"imad_per_s": peak, "sms": sms, "sm_mhz": mhz,
+                       "per_sm_clk": IMAD_PER_SM_CLK, "algorithmic_imad_per_product": 2},
+          "sizes": rows})
+
+    # -- mixed ragged batch: one persistent bucketed kernel vs one launch per size
+    w = W.ragged_mixed()
+    n = w["op"].size
+    desc = np.zeros(n, dtype=[("op", "<u4"), ("m", "<u4"), ("a_off", "<u8"), ("b_off", "<u8"),
+                              ("r_off", "<u8")])
+    desc["op"], desc["m"] = w["op"], w["m"]
+    desc["a_off"] = desc["b_off"] = w["a_off"][:-1]
+    desc["r_off"] = w["r_off"][:-1]
+    ddesc = torch.from_numpy(desc.view(np.uint8).copy()).cuda()
+    a, b = dv(w["a"]), dv(w["b"])
+    r = torch.zeros(int(w["r_off"][-1]), dtype=torch.int32, device="cuda")
+    cr = torch.zeros(n, dtype=torch.int32, device="cuda")
+    t_mixed = _event_ms(lambda: dot.mixed_ragged(ddesc, a, b, r, cr, ctx=ctx), 20, stream)
+    wr, wc = oracle.mixed(desc["op"], desc["m"], desc["a_off"], desc["b_off"], desc["r_off"],
+                          w["a"], w["b"], w["r_off"][-1])
+    ok = np.array_equal(hs(r), wr) and np.array_equal(hs(cr), wc)
+    # one launch per (op, size): operands regrouped contiguously beforehand
+    groups = []
+    for opc in (W.OP_ADD, W.OP_SUB, W.OP_MUL):
+        for m in np.unique(w["m"][w["op"] == opc]):
+            idx = np.nonzero((w["op"] == opc) & (w["m"] == m))[0]
+            rows_a = np.stack([w["a"][int(w["a_off"][i]):int(w["a_off"][i]) + m] for i in idx])
+            rows_b = np.stack([w["b"][int(w["a_off"][i]):int(w["a_off"][i]) + m] for i in idx])
+            ga, gb = dv(rows_a), dv(rows_b)
+            out = torch.empty((idx.size, 2 * m if opc == W.OP_MUL else m), dtype=torch.int32,
+                              device="cuda")
+            gc = torch.empty(idx.size, dtype=torch.int32, device="cuda")
+            groups.append((opc, ga, gb, out, gc))
+
+    def per_size():
+        for opc, ga, gb, out, gc in groups:
+            if opc == W.OP_MUL:
+                dot.mul(ga, gb, out, ctx=ctx)
+            elif opc == W.OP_ADD:
+                dot.add(ga, gb, out, gc, ctx=ctx)
+            else:
+                dot.sub(ga, gb, out, gc, ctx=ctx)
+    t_per = _event_ms(per_size, 5, stream)
+    prods = int((w["m"][w["op"] == W.OP_MUL].astype(np.int64) ** 2).sum())
+    emit({"workload": "ragged mixed: 200k ops, 30/30/40 add/sub/mul, 128..16384 bits",
+          "bit_exact": bool(ok), "ms_persistent_graph": round(t_mixed, 4),
+          "gop_s": round(n / (t_mixed * 1e-3) / 1e9, 4),
+          "ms_one_launch_per_size": round(t_per, 4), "launches_per_size": len(groups),
+          "speedup_vs_per_size": round(t_per / t_mixed, 3),
+          "roofline": {"bound": "alu", "achieved_imad_per_s": 2.0 * prods / (t_mixed * 1e-3),
+                       "peak": peak, "frac": round(2.0 * prods / (t_mixed * 1e-3) / peak, 4)}})
+
+    # -- shared operand: INT32 column-sum path
+    f, bb = W.shared_operand()
+    a = dv(np.ascontiguousarray(np.broadcast_to(f, bb.shape)))
+    b = dv(bb)
+    p = torch.empty((bb.shape[0], 128), dtype=torch.int32, device="cuda")
+    t_int = _event_ms(lambda: dot.mul(a, b, p, ctx=ctx), 50, stream)
+    sel = np.arange(0, bb.shape[0], 97)
+    ok = np.array_equal(hs(p)[sel], oracle.mul(np.broadcast_to(f, (sel.size, 64)), bb[sel]))
+    emit({"workload": "shared operand: fixed 2048-bit x 2^16 2048-bit", "bit_exact_sample": bool(ok),
+          "ms_int32": round(t_int, 4), "gop_s_int32": round(bb.shape[0] / (t_int * 1e-3) / 1e9, 4)})
+    assert ctx.check() == dot.OK
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--suite", action="store_true",
+                    help="measure every workload row (one JSON line each) instead of the bench step")
     ap.add_argument("--profile-case", action="store_true",
                     help="run only the small ncu case of the dominant kernel")
     ap.add_argument("--launches", type=int, default=3)
@@ -421,10 +590,10 @@ def main():
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     rank, world, local = dist_info()
-    if args.profile_case:
+    if args.profile_case or args.suite:
         from paper_2604_21566_gb300 import build as B
         B.build()
-        profile_case(args)
+        (suite if args.suite else profile_case)(args)
         return
     if args.impl == "reference":
         reference_arm(args, rank, world)
