@@ -177,6 +177,38 @@ DOT_API dot_status_t dot_sub_host(dot_ctx_t ctx, const uint32_t *a, const uint32
 DOT_API dot_status_t dot_mul_host(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b,
                                   uint32_t *p, size_t m, size_t batch, dot_stream_t stream);
 
+/* ------------------------------------------------- allocation-free add --- */
+
+/* dot_add without any device allocation, for callers that must not call
+ * cudaMalloc: code that runs inside another allocator's callbacks, in a
+ * latency-critical or signal-handling path that may not block on the driver's
+ * memory manager, or in a process whose device memory is all owned by a pool
+ * it cannot share.  (The paper has no counterpart: it is a packaging choice of
+ * this library.)  Same result and layout as dot_add: s[k] + carry_out[k] X^m
+ * = a[k] + b[k]; a, b, s, carry_out and stream belong to CUDA device `device`.
+ *
+ * No dot_ctx_t is used (creating one allocates).  The scratch of the tiled
+ * look-back kernel is a fixed device array inside the library, which every GPU
+ * that loads libdot holds until the process exits: 4 + 16384 64-bit words
+ * (128 KiB), i.e. at most 16384 tiles per call, where one op of m limbs spans
+ * ceil(m / tile) tiles of 1024 to 4096 limbs (256 to 1024 limbs when m % 4 != 0
+ * or a row is not 16-byte aligned); larger calls return DOT_EUNSUPPORTED
+ * before any launch.  Ops of at most 512 limbs (128 for the unaligned case)
+ * run without tiles and have no limit on batch.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, which may load the library's kernels onto the
+ * device); make that first call before any stream capture.  Every call
+ * shares the one array: a call clears the part it uses on `stream` before
+ * its kernel runs, and calls whose kernels overlap on the GPU (different
+ * streams, or different host threads on one device) race and may give wrong
+ * results.  There is no context to record a device-side wait timeout in:
+ * such a timeout (a wait of over 2 s, which a healthy GPU never reaches) is
+ * not reported.  Argument errors are returned as by dot_add. */
+DOT_API dot_status_t dot_add_noalloc(int device, const uint32_t *a, const uint32_t *b,
+                                     uint32_t *s, uint32_t *carry_out, size_t m, size_t batch,
+                                     dot_stream_t stream);
+
 /* ------------------------------------------------------- introspection --- */
 
 /* The launch plan the library uses for one batched call (host logic only,

@@ -391,3 +391,114 @@ DOT_API dot_status_t dot_sub_ragged(dot_ctx_t ctx, const uint32_t *a, const uint
 }
 
 }  // extern "C"
+
+// ====================================================== allocation-free add
+// dot_add_noalloc: the same addition as dot_add, for callers that cannot call
+// cudaMalloc at all -- code running where the allocator is off limits (inside
+// another allocator's callback, a signal or real-time path that may not block
+// on the driver's memory manager, or a host that has handed all device memory
+// to a pool it does not share).  It needs no dot_ctx_t (creating one
+// allocates).  The look-back scratch of the tiled kernel lives instead in the
+// fixed device array below, which every GPU that loads this library holds
+// until the process exits.
+#define DOT_NOALLOC_HDR 4          // [0] tile ticket, [1] blocks done, [2] epoch, [3] status word
+#define DOT_NOALLOC_MAX_TILES 16384
+#define DOT_NOALLOC_MAX_DEVICES 64
+
+static __device__ __align__(256) unsigned long long
+    g_noalloc_scratch[DOT_NOALLOC_HDR + DOT_NOALLOC_MAX_TILES];
+
+// device address of g_noalloc_scratch, looked up once per device
+static unsigned long long *g_noalloc_addr[DOT_NOALLOC_MAX_DEVICES];
+static int g_noalloc_sms[DOT_NOALLOC_MAX_DEVICES];
+
+static dot_status_t noalloc_setup(int device)
+{
+    if (g_noalloc_addr[device]) return DOT_OK;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return DOT_ECUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return DOT_ECUDA;
+    g_noalloc_sms[device] = sms;
+    g_noalloc_addr[device] = (unsigned long long *)p;
+    return DOT_OK;
+}
+
+template <bool SUB, int SEG>
+static dot_status_t noalloc_launch(int sms, unsigned long long *scratch, const dot_plan_t &pl,
+                                   const uint32_t *a, const uint32_t *b, uint32_t *s, uint32_t *cout,
+                                   size_t m, size_t batch, cudaStream_t st)
+{
+    if (pl.kernel == DOT_K_ADDSUB_WARP) {
+        const int lpo = pl.lanes_per_op, nch = pl.chunks, opw = 32 / lpo;
+        const int U = (nch == 1) ? 2 : 1;
+        const size_t need = dot_ceil_div(dot_ceil_div(batch, (size_t)opw * U), WARP_KERNEL_THREADS / 32);
+        const void *fn = nch == 1 ? (const void *)addsub_warp_kernel<SUB, SEG, 1, 2>
+                       : nch == 2 ? (const void *)addsub_warp_kernel<SUB, SEG, 2, 1>
+                                  : (const void *)addsub_warp_kernel<SUB, SEG, 4, 1>;
+        const size_t cap = (size_t)sms * dot_blocks_per_sm(fn, WARP_KERNEL_THREADS, 0);
+        const unsigned grid = (unsigned)(need < cap ? need : cap);
+        if (nch == 1)
+            addsub_warp_kernel<SUB, SEG, 1, 2><<<grid, WARP_KERNEL_THREADS, 0, st>>>(a, b, s, cout, m, batch, lpo, nch);
+        else if (nch == 2)
+            addsub_warp_kernel<SUB, SEG, 2, 1><<<grid, WARP_KERNEL_THREADS, 0, st>>>(a, b, s, cout, m, batch, lpo, nch);
+        else
+            addsub_warp_kernel<SUB, SEG, 4, 1><<<grid, WARP_KERNEL_THREADS, 0, st>>>(a, b, s, cout, m, batch, lpo, nch);
+        return cudaGetLastError() == cudaSuccess ? DOT_OK : DOT_ECUDA;
+    }
+    const size_t tiles = (size_t)pl.tiles * batch;
+    // the counters, epoch, status and this call's tile states must start at zero
+    if (cudaMemsetAsync(scratch, 0, (DOT_NOALLOC_HDR + tiles) * sizeof(unsigned long long), st) != cudaSuccess)
+        return DOT_ECUDA;
+    LookbackArgs lb;
+    lb.counters = scratch;
+    lb.status = (uint32_t *)(scratch + 3);
+    lb.state = scratch + DOT_NOALLOC_HDR;
+    lb.wait_limit_ns = 2000000000ull;
+    lb.skip_tile = -1;
+    const void *fn = pl.chunks == 1 ? (const void *)addsub_tile_kernel<SUB, SEG, 1>
+                   : pl.chunks == 2 ? (const void *)addsub_tile_kernel<SUB, SEG, 2>
+                                    : (const void *)addsub_tile_kernel<SUB, SEG, 4>;
+    const size_t cap = (size_t)sms * dot_blocks_per_sm(fn, DOT_TILE_THREADS, 0);
+    const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
+    const unsigned long long tpo = pl.tiles;
+    if (pl.chunks == 1)
+        addsub_tile_kernel<SUB, SEG, 1><<<grid, DOT_TILE_THREADS, 0, st>>>(a, b, s, cout, m, batch, tpo, lb);
+    else if (pl.chunks == 2)
+        addsub_tile_kernel<SUB, SEG, 2><<<grid, DOT_TILE_THREADS, 0, st>>>(a, b, s, cout, m, batch, tpo, lb);
+    else
+        addsub_tile_kernel<SUB, SEG, 4><<<grid, DOT_TILE_THREADS, 0, st>>>(a, b, s, cout, m, batch, tpo, lb);
+    return cudaGetLastError() == cudaSuccess ? DOT_OK : DOT_ECUDA;
+}
+
+extern "C" DOT_API dot_status_t dot_add_noalloc(int device, const uint32_t *a, const uint32_t *b, uint32_t *s,
+                                                uint32_t *carry_out, size_t m, size_t batch, dot_stream_t stream)
+{
+    if (device < 0 || device >= DOT_NOALLOC_MAX_DEVICES) return DOT_EINVAL;
+    if (batch == 0) return DOT_OK;
+    if (!carry_out || (m && (!a || !b || !s))) return DOT_EINVAL;
+    if (m > SIZE_MAX / 4 / batch) return DOT_EINVAL;
+    const size_t bytes = m * batch * 4;
+    if (partial_overlap(s, bytes, a, bytes) || partial_overlap(s, bytes, b, bytes)) return DOT_EINVAL;
+    if (any_overlap(carry_out, batch * 4, s, bytes) || any_overlap(carry_out, batch * 4, a, bytes) ||
+        any_overlap(carry_out, batch * 4, b, bytes))
+        return DOT_EINVAL;
+    const bool vec = (m % 4 == 0) && aligned16(a) && aligned16(b) && aligned16(s);
+    dot_plan_t pl;
+    dot_status_t rc = dot_make_plan(DOT_OP_ADD, m, batch, vec, &pl);
+    if (rc != DOT_OK) return rc;
+    if (pl.kernel == DOT_K_ADDSUB_TILE && (pl.tiles > DOT_NOALLOC_MAX_TILES ||
+                                           batch > DOT_NOALLOC_MAX_TILES / pl.tiles))
+        return DOT_EUNSUPPORTED;   // more tiles than the fixed scratch array holds
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return DOT_ECUDA;
+    if (cur != device && cudaSetDevice(device) != cudaSuccess) return DOT_ECUDA;
+    rc = noalloc_setup(device);
+    if (rc != DOT_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (m == 0) return cudaMemsetAsync(carry_out, 0, batch * 4, st) == cudaSuccess ? DOT_OK : DOT_ECUDA;
+    return vec ? noalloc_launch<false, 4>(g_noalloc_sms[device], g_noalloc_addr[device], pl, a, b, s,
+                                          carry_out, m, batch, st)
+               : noalloc_launch<false, 1>(g_noalloc_sms[device], g_noalloc_addr[device], pl, a, b, s,
+                                          carry_out, m, batch, st);
+}

@@ -71,6 +71,7 @@ _SIGS = {
     "dot_add_host": (_st, [_vp, _vp, _vp, _vp, _vp, _sz, _sz, _vp]),
     "dot_sub_host": (_st, [_vp, _vp, _vp, _vp, _vp, _sz, _sz, _vp]),
     "dot_mul_host": (_st, [_vp, _vp, _vp, _vp, _sz, _sz, _vp]),
+    "dot_add_noalloc": (_st, [ctypes.c_int, _vp, _vp, _vp, _vp, _sz, _sz, _vp]),
 }
 
 _lib = None
@@ -281,6 +282,22 @@ def mixed_ragged(desc, a, b, r, carry, ctx=None, stream=None):
     _chk(lib().dot_mixed_ragged(ctx.handle, _ptr(desc), nops, _ptr(a), _ptr(b), _ptr(r), _ptr(carry),
                                 _stream(stream)), "dot_mixed_ragged")
     return r, carry
+
+
+def add_noalloc(a, b, out=None, carry=None, stream=None):
+    """dot_add_noalloc: the addition of add() through the entry point that
+    performs no device allocation (its scratch is a fixed array inside the
+    library; no context).  Calls must not overlap on the GPU."""
+    import torch
+    out = torch.empty_like(a) if out is None else out
+    carry = torch.empty(a.shape[0], dtype=a.dtype, device=a.device) if carry is None else carry
+    _limb_tensor(a, "a"), _limb_tensor(b, "b"), _limb_tensor(out, "out"), _limb_tensor(carry, "carry")
+    if a.dim() != 2 or a.shape != b.shape or out.shape != a.shape or carry.numel() != a.shape[0]:
+        raise ValueError("dot_add_noalloc: a, b, out must be [batch, m]; carry [batch]")
+    batch, m = a.shape
+    _chk(lib().dot_add_noalloc(a.device.index, _ptr(a), _ptr(b), _ptr(out), _ptr(carry), m, batch,
+                               _stream(stream)), "dot_add_noalloc")
+    return out, carry
 
 
 # ------------------------------------------------- host-buffer variants
