@@ -36,15 +36,24 @@ sys.path.insert(0, ROOT)
 METRIC = "Gop/s bit-exact add/sub/mul per operand size; % HBM or int-pipe roofline"
 WORKLOAD = "add/sub bandwidth: 2^20 x 4096-bit + 64 x 2^22-bit operand pairs, add and sub"
 PROFILE = os.path.join(ROOT, "profiles", "addsub_warp_kernel_4096bit.md")
-KERNEL_SOURCES = [os.path.join(ROOT, "paper_2604_21566_gb300", "csrc", f)
-                  for f in ("dot_addsub.cu", "dot_internal.cuh", "dot_plan.h")]
+CSRC = os.path.join(ROOT, "paper_2604_21566_gb300", "csrc")
+KERNEL_HEADERS = ("dot_internal.cuh", "dot_addsub.cuh", "dot_plan.h")
 
 
 def kernel_source_hash() -> str:
+    """Hash of the dominant kernel's code: its headers plus the text of
+    addsub_warp_kernel and its launcher in dot_addsub.cu."""
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
-        with open(p, "rb") as f:
-            h.update(f.read())
+    for f in KERNEL_HEADERS:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    src = open(os.path.join(CSRC, "dot_addsub.cu")).read()
+    lo = src.index("// ======================================================= warp kernel (1)")
+    hi = src.index("// ================================================= tiled kernel (2)")
+    h.update(src[lo:hi].encode())
+    lo = src.index("template <bool SUB, int SEG>\nstatic cudaError_t launch_warp")
+    hi = src.index("template <bool SUB, int SEG>\nstatic dot_status_t launch_tile")
+    h.update(src[lo:hi].encode())
     return h.hexdigest()[:16]
 
 
@@ -398,21 +407,32 @@ def reference_arm(args, rank, world):
 
 
 def profile_case(args):
-    """Small case for ncu: dot_add on 2^18 pairs of 4096-bit operands
-    (403 MB of algorithmic traffic, larger than L2), a few launches."""
+    """Small cases for ncu, a few launches each:
+    add  -- dot_add on 2^18 pairs of 4096-bit operands (403 MB, > L2);
+    long -- dot_add on 16 pairs of 2^22-bit operands (25 MB, look-back tiles);
+    mul  -- dot_mul on 2^16 pairs of 8192-bit operands (256 MB in + out)."""
     import torch
     from paper_2604_21566_gb300 import dot
     from paper_2604_21566_gb300 import workloads as W
     torch.cuda.set_device(0)
-    d = W.addsub_bandwidth(short_batch=1 << 18, long_batch=0)
-    x, y = d["add_short"]
+    ctx = dot.Context(0)
+    if args.case == "mul":
+        x, y, _ = W.batched_mul(256)
+    elif args.case == "long":
+        x, y = W.addsub_bandwidth(short_batch=0, long_batch=16)["add_long"]
+    else:
+        x, y = W.addsub_bandwidth(short_batch=1 << 18, long_batch=0)["add_short"]
     a = torch.from_numpy(x.view(np.int32)).cuda()
     b = torch.from_numpy(y.view(np.int32)).cuda()
-    s = torch.empty_like(a)
-    c = torch.empty(a.shape[0], dtype=torch.int32, device="cuda")
-    ctx = dot.Context(0)
-    for _ in range(args.launches):
-        dot.add(a, b, out=s, carry=c, ctx=ctx)
+    if args.case == "mul":
+        p = torch.empty((x.shape[0], 2 * x.shape[1]), dtype=torch.int32, device="cuda")
+        for _ in range(args.launches):
+            dot.mul(a, b, p, ctx=ctx)
+    else:
+        s = torch.empty_like(a)
+        c = torch.empty(a.shape[0], dtype=torch.int32, device="cuda")
+        for _ in range(args.launches):
+            dot.add(a, b, out=s, carry=c, ctx=ctx)
     torch.cuda.synchronize()
     assert ctx.check() == dot.OK
     print("profile case done")
@@ -470,105 +490,112 @@ def suite(args):
         d["suite"] = True
         print(json.dumps(d), flush=True)
 
-    # -- correctness mix: 4096 x 1024-bit, latency-bound
-    d = W.correctness_mix()
-    a, b = dv(d["x"]), dv(d["y"])
-    asub, bsub = dv(d["a_sub"]), dv(d["b_sub"])
-    s = torch.empty_like(a)
-    c = torch.empty(a.shape[0], dtype=torch.int32, device="cuda")
-    p = torch.empty((a.shape[0], 64), dtype=torch.int32, device="cuda")
-    t_add = _event_ms(lambda: dot.add(a, b, s, c, ctx=ctx), 200, stream)
-    ok = np.array_equal(hs(s), oracle.add(d["x"], d["y"])[0])
-    t_sub = _event_ms(lambda: dot.sub(asub, bsub, s, c, ctx=ctx), 200, stream)
-    ok &= np.array_equal(hs(s), oracle.sub(d["a_sub"], d["b_sub"])[0])
-    t_mul = _event_ms(lambda: dot.mul(a, b, p, ctx=ctx), 200, stream)
-    ok &= np.array_equal(hs(p), oracle.mul(d["x"], d["y"], threads=oracle.cores()))
-    emit({"workload": "correctness mix: 4096 x 1024-bit (m=32), add/sub/mul", "bit_exact": bool(ok),
-          "us_per_call": {"add": round(t_add * 1e3, 2), "sub": round(t_sub * 1e3, 2),
-                          "mul": round(t_mul * 1e3, 2)},
-          "gop_s": {"add": round(4096 / t_add / 1e6, 3), "sub": round(4096 / t_sub / 1e6, 3),
-                    "mul": round(4096 / t_mul / 1e6, 3)}})
+    def want(name):
+        return not args.only or name in args.only.split(",")
 
-    # -- batched multiply at fixed size
-    rows = []
-    for m in W.BATCHED_MUL_SIZES:
-        x, y, _ = W.batched_mul(m)
-        a, b = dv(x), dv(y)
-        p = torch.empty((x.shape[0], 2 * m), dtype=torch.int32, device="cuda")
-        ms = _event_ms(lambda: dot.mul(a, b, p, ctx=ctx), 20, stream)
-        sel = np.random.default_rng(m).integers(0, x.shape[0], 512)
-        ok = np.array_equal(hs(p)[sel], oracle.mul(x[sel], y[sel]))
-        prods = x.shape[0] * m * m
-        imad = 2.0 * prods / (ms * 1e-3)
-        rows.append({"m_limbs": m, "bits": 32 * m, "ops": x.shape[0], "ms": round(ms, 4),
-                     "gop_s": round(x.shape[0] / (ms * 1e-3) / 1e9, 4),
-                     "tera_limb_products_s": round(prods / (ms * 1e-3) / 1e12, 3),
-                     "GB_s": round(16 * m * x.shape[0] / (ms * 1e-3) / 1e9, 1),
-                     "roofline": {"bound": "alu", "achieved_imad_per_s": imad, "peak": peak,
-                                  "frac": round(imad / peak, 4)},
-                     "bit_exact_sample": bool(ok)})
-    emit({"workload": "batched multiply: 2^16 pairs at 256/1024/4096/8192 bits",
-          "int_peak": {"imad_per_s": peak, "sms": sms, "sm_mhz": mhz,
-                       "per_sm_clk": IMAD_PER_SM_CLK, "algorithmic_imad_per_product": 2},
-          "sizes": rows})
+    if want("mix"):
+        # -- correctness mix: 4096 x 1024-bit, latency-bound
+        d = W.correctness_mix()
+        a, b = dv(d["x"]), dv(d["y"])
+        asub, bsub = dv(d["a_sub"]), dv(d["b_sub"])
+        s = torch.empty_like(a)
+        c = torch.empty(a.shape[0], dtype=torch.int32, device="cuda")
+        p = torch.empty((a.shape[0], 64), dtype=torch.int32, device="cuda")
+        t_add = _event_ms(lambda: dot.add(a, b, s, c, ctx=ctx), 200, stream)
+        ok = np.array_equal(hs(s), oracle.add(d["x"], d["y"])[0])
+        t_sub = _event_ms(lambda: dot.sub(asub, bsub, s, c, ctx=ctx), 200, stream)
+        ok &= np.array_equal(hs(s), oracle.sub(d["a_sub"], d["b_sub"])[0])
+        t_mul = _event_ms(lambda: dot.mul(a, b, p, ctx=ctx), 200, stream)
+        ok &= np.array_equal(hs(p), oracle.mul(d["x"], d["y"], threads=oracle.cores()))
+        emit({"workload": "correctness mix: 4096 x 1024-bit (m=32), add/sub/mul", "bit_exact": bool(ok),
+              "us_per_call": {"add": round(t_add * 1e3, 2), "sub": round(t_sub * 1e3, 2),
+                              "mul": round(t_mul * 1e3, 2)},
+              "gop_s": {"add": round(4096 / t_add / 1e6, 3), "sub": round(4096 / t_sub / 1e6, 3),
+                        "mul": round(4096 / t_mul / 1e6, 3)}})
 
-    # -- mixed ragged batch: one persistent bucketed kernel vs one launch per size
-    w = W.ragged_mixed()
-    n = w["op"].size
-    desc = np.zeros(n, dtype=[("op", "<u4"), ("m", "<u4"), ("a_off", "<u8"), ("b_off", "<u8"),
-                              ("r_off", "<u8")])
-    desc["op"], desc["m"] = w["op"], w["m"]
-    desc["a_off"] = desc["b_off"] = w["a_off"][:-1]
-    desc["r_off"] = w["r_off"][:-1]
-    ddesc = torch.from_numpy(desc.view(np.uint8).copy()).cuda()
-    a, b = dv(w["a"]), dv(w["b"])
-    r = torch.zeros(int(w["r_off"][-1]), dtype=torch.int32, device="cuda")
-    cr = torch.zeros(n, dtype=torch.int32, device="cuda")
-    t_mixed = _event_ms(lambda: dot.mixed_ragged(ddesc, a, b, r, cr, ctx=ctx), 20, stream)
-    wr, wc = oracle.mixed(desc["op"], desc["m"], desc["a_off"], desc["b_off"], desc["r_off"],
-                          w["a"], w["b"], w["r_off"][-1])
-    ok = np.array_equal(hs(r), wr) and np.array_equal(hs(cr), wc)
-    # one launch per (op, size): operands regrouped contiguously beforehand
-    groups = []
-    for opc in (W.OP_ADD, W.OP_SUB, W.OP_MUL):
-        for m in np.unique(w["m"][w["op"] == opc]):
-            idx = np.nonzero((w["op"] == opc) & (w["m"] == m))[0]
-            rows_a = np.stack([w["a"][int(w["a_off"][i]):int(w["a_off"][i]) + m] for i in idx])
-            rows_b = np.stack([w["b"][int(w["a_off"][i]):int(w["a_off"][i]) + m] for i in idx])
-            ga, gb = dv(rows_a), dv(rows_b)
-            out = torch.empty((idx.size, 2 * m if opc == W.OP_MUL else m), dtype=torch.int32,
-                              device="cuda")
-            gc = torch.empty(idx.size, dtype=torch.int32, device="cuda")
-            groups.append((opc, ga, gb, out, gc))
+    if want("mul"):
+        # -- batched multiply at fixed size
+        rows = []
+        for m in W.BATCHED_MUL_SIZES:
+            x, y, _ = W.batched_mul(m)
+            a, b = dv(x), dv(y)
+            p = torch.empty((x.shape[0], 2 * m), dtype=torch.int32, device="cuda")
+            ms = _event_ms(lambda: dot.mul(a, b, p, ctx=ctx), 20, stream)
+            sel = np.random.default_rng(m).integers(0, x.shape[0], 512)
+            ok = np.array_equal(hs(p)[sel], oracle.mul(x[sel], y[sel]))
+            prods = x.shape[0] * m * m
+            imad = 2.0 * prods / (ms * 1e-3)
+            rows.append({"m_limbs": m, "bits": 32 * m, "ops": x.shape[0], "ms": round(ms, 4),
+                         "gop_s": round(x.shape[0] / (ms * 1e-3) / 1e9, 4),
+                         "tera_limb_products_s": round(prods / (ms * 1e-3) / 1e12, 3),
+                         "GB_s": round(16 * m * x.shape[0] / (ms * 1e-3) / 1e9, 1),
+                         "roofline": {"bound": "alu", "achieved_imad_per_s": imad, "peak": peak,
+                                      "frac": round(imad / peak, 4)},
+                         "bit_exact_sample": bool(ok)})
+        emit({"workload": "batched multiply: 2^16 pairs at 256/1024/4096/8192 bits",
+              "int_peak": {"imad_per_s": peak, "sms": sms, "sm_mhz": mhz,
+                           "per_sm_clk": IMAD_PER_SM_CLK, "algorithmic_imad_per_product": 2},
+              "sizes": rows})
 
-    def per_size():
-        for opc, ga, gb, out, gc in groups:
-            if opc == W.OP_MUL:
-                dot.mul(ga, gb, out, ctx=ctx)
-            elif opc == W.OP_ADD:
-                dot.add(ga, gb, out, gc, ctx=ctx)
-            else:
-                dot.sub(ga, gb, out, gc, ctx=ctx)
-    t_per = _event_ms(per_size, 5, stream)
-    prods = int((w["m"][w["op"] == W.OP_MUL].astype(np.int64) ** 2).sum())
-    emit({"workload": "ragged mixed: 200k ops, 30/30/40 add/sub/mul, 128..16384 bits",
-          "bit_exact": bool(ok), "ms_persistent_graph": round(t_mixed, 4),
-          "gop_s": round(n / (t_mixed * 1e-3) / 1e9, 4),
-          "ms_one_launch_per_size": round(t_per, 4), "launches_per_size": len(groups),
-          "speedup_vs_per_size": round(t_per / t_mixed, 3),
-          "roofline": {"bound": "alu", "achieved_imad_per_s": 2.0 * prods / (t_mixed * 1e-3),
-                       "peak": peak, "frac": round(2.0 * prods / (t_mixed * 1e-3) / peak, 4)}})
+    if want("mixed"):
+        # -- mixed ragged batch: one persistent bucketed kernel vs one launch per size
+        w = W.ragged_mixed()
+        n = w["op"].size
+        desc = np.zeros(n, dtype=[("op", "<u4"), ("m", "<u4"), ("a_off", "<u8"), ("b_off", "<u8"),
+                                  ("r_off", "<u8")])
+        desc["op"], desc["m"] = w["op"], w["m"]
+        desc["a_off"] = desc["b_off"] = w["a_off"][:-1]
+        desc["r_off"] = w["r_off"][:-1]
+        ddesc = torch.from_numpy(desc.view(np.uint8).copy()).cuda()
+        a, b = dv(w["a"]), dv(w["b"])
+        r = torch.zeros(int(w["r_off"][-1]), dtype=torch.int32, device="cuda")
+        cr = torch.zeros(n, dtype=torch.int32, device="cuda")
+        t_mixed = _event_ms(lambda: dot.mixed_ragged(ddesc, a, b, r, cr, ctx=ctx), 20, stream)
+        wr, wc = oracle.mixed(desc["op"], desc["m"], desc["a_off"], desc["b_off"], desc["r_off"],
+                              w["a"], w["b"], w["r_off"][-1])
+        ok = np.array_equal(hs(r), wr) and np.array_equal(hs(cr), wc)
+        # one launch per (op, size): operands regrouped contiguously beforehand
+        groups = []
+        for opc in (W.OP_ADD, W.OP_SUB, W.OP_MUL):
+            for m in np.unique(w["m"][w["op"] == opc]):
+                idx = np.nonzero((w["op"] == opc) & (w["m"] == m))[0]
+                rows_a = np.stack([w["a"][int(w["a_off"][i]):int(w["a_off"][i]) + m] for i in idx])
+                rows_b = np.stack([w["b"][int(w["a_off"][i]):int(w["a_off"][i]) + m] for i in idx])
+                ga, gb = dv(rows_a), dv(rows_b)
+                out = torch.empty((idx.size, 2 * m if opc == W.OP_MUL else m), dtype=torch.int32,
+                                  device="cuda")
+                gc = torch.empty(idx.size, dtype=torch.int32, device="cuda")
+                groups.append((opc, ga, gb, out, gc))
 
-    # -- shared operand: INT32 column-sum path
-    f, bb = W.shared_operand()
-    a = dv(np.ascontiguousarray(np.broadcast_to(f, bb.shape)))
-    b = dv(bb)
-    p = torch.empty((bb.shape[0], 128), dtype=torch.int32, device="cuda")
-    t_int = _event_ms(lambda: dot.mul(a, b, p, ctx=ctx), 50, stream)
-    sel = np.arange(0, bb.shape[0], 97)
-    ok = np.array_equal(hs(p)[sel], oracle.mul(np.broadcast_to(f, (sel.size, 64)), bb[sel]))
-    emit({"workload": "shared operand: fixed 2048-bit x 2^16 2048-bit", "bit_exact_sample": bool(ok),
-          "ms_int32": round(t_int, 4), "gop_s_int32": round(bb.shape[0] / (t_int * 1e-3) / 1e9, 4)})
+        def per_size():
+            for opc, ga, gb, out, gc in groups:
+                if opc == W.OP_MUL:
+                    dot.mul(ga, gb, out, ctx=ctx)
+                elif opc == W.OP_ADD:
+                    dot.add(ga, gb, out, gc, ctx=ctx)
+                else:
+                    dot.sub(ga, gb, out, gc, ctx=ctx)
+        t_per = _event_ms(per_size, 5, stream)
+        prods = int((w["m"][w["op"] == W.OP_MUL].astype(np.int64) ** 2).sum())
+        emit({"workload": "ragged mixed: 200k ops, 30/30/40 add/sub/mul, 128..16384 bits",
+              "bit_exact": bool(ok), "ms_persistent_graph": round(t_mixed, 4),
+              "gop_s": round(n / (t_mixed * 1e-3) / 1e9, 4),
+              "ms_one_launch_per_size": round(t_per, 4), "launches_per_size": len(groups),
+              "speedup_vs_per_size": round(t_per / t_mixed, 3),
+              "roofline": {"bound": "alu", "achieved_imad_per_s": 2.0 * prods / (t_mixed * 1e-3),
+                           "peak": peak, "frac": round(2.0 * prods / (t_mixed * 1e-3) / peak, 4)}})
+
+    if want("shared"):
+        # -- shared operand: INT32 column-sum path
+        f, bb = W.shared_operand()
+        a = dv(np.ascontiguousarray(np.broadcast_to(f, bb.shape)))
+        b = dv(bb)
+        p = torch.empty((bb.shape[0], 128), dtype=torch.int32, device="cuda")
+        t_int = _event_ms(lambda: dot.mul(a, b, p, ctx=ctx), 50, stream)
+        sel = np.arange(0, bb.shape[0], 97)
+        ok = np.array_equal(hs(p)[sel], oracle.mul(np.broadcast_to(f, (sel.size, 64)), bb[sel]))
+        emit({"workload": "shared operand: fixed 2048-bit x 2^16 2048-bit", "bit_exact_sample": bool(ok),
+              "ms_int32": round(t_int, 4), "gop_s_int32": round(bb.shape[0] / (t_int * 1e-3) / 1e9, 4)})
     assert ctx.check() == dot.OK
     ctx.close()
 
@@ -580,6 +607,9 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run only the small ncu case of the dominant kernel")
     ap.add_argument("--launches", type=int, default=3)
+    ap.add_argument("--only", default="", help="--suite rows to run: mix,mul,mixed,shared")
+    ap.add_argument("--case", choices=["add", "long", "mul"], default="add",
+                    help="which kernel --profile-case runs")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)

@@ -7,13 +7,14 @@
 //  * Column sums (Alg. 2 Phases 1-4).  Thread t of an op's group owns two
 //    blocks of R consecutive columns, [tR, tR+R) and [m' + tR, m' + tR + R)
 //    (m' = m rounded up to R), so every thread does the same m' R products:
-//    column c has c+1 pairs and column m'+c has m'-1-c.  For each i it adds
-//    the R products A_i * B_{c-i} of its block into a positional accumulator
-//    W = sum_k S_{c0+k} X^k of R+2 words.  The products of even k occupy
-//    disjoint word pairs (k, k+1), and so do those of odd k, so each half is
-//    one unbroken mad.lo.cc / madc.hi.cc carry chain: 2 IMAD-class
-//    instructions per product plus 3 per row.  Phase 1's gather is index
-//    arithmetic on operands staged in shared memory; nothing is materialised.
+//    column c has c+1 pairs and column m'+c has m'-1-c.  For each i it forms
+//    the R products A_i * B_{c-i} of its block independently (low and high
+//    halves: 2 multiplies on the FMA pipe) and adds each into its column's
+//    three-word sum (3 adds on the ALU pipe, in parallel with the next
+//    multiplies).  At the end of the block the R column sums become one
+//    positional value W = sum_k S_{c0+k} X^k of R+2 words.  Phase 1's gather
+//    is index arithmetic on operands staged in shared memory; nothing is
+//    materialised.
 //  * Carry resolution (Alg. 2 Phase 5), made parallel.  A block's two top
 //    words overlap the next block's two bottom words, so the product is
 //    L + H: L the blocks' low R words side by side, H their overflow words
@@ -27,7 +28,7 @@
 
 // Batched product: runs of T = m'/R lanes, 32/T ops per warp.
 template <int R>
-__global__ void __launch_bounds__(MUL_WARPS * 32)
+__global__ void __launch_bounds__(MUL_WARPS * 32, dot_mul_min_blocks(R))
 mul_batched_kernel(const uint32_t *a, const uint32_t *b, uint32_t *p, int m, int mp, int T,
                    size_t batch, int vec_in, int vec_out)
 {
@@ -66,7 +67,7 @@ mul_batched_kernel(const uint32_t *a, const uint32_t *b, uint32_t *p, int m, int
 // are left to a kernel with larger R (size classes), m_k > DOT_MUL_MAX_LIMBS
 // records DOT_EUNSUPPORTED.
 template <int R>
-__global__ void __launch_bounds__(MUL_WARPS * 32)
+__global__ void __launch_bounds__(MUL_WARPS * 32, dot_mul_min_blocks(R))
 mul_ragged_kernel(const uint32_t *a, const uint32_t *b, uint32_t *p, const uint64_t *off,
                   const uint64_t *poff, size_t batch, int m_min, int m_max, uint32_t *status)
 {

@@ -5,75 +5,49 @@
 #include "dot_internal.cuh"
 
 #define MUL_WARPS 4
+// Resident blocks per SM the compiler must allow (caps registers per thread):
+// 6 blocks of 4 warps fit R <= 8 in 80 registers without spills; R = 16
+// needs its ~170 registers.
+__host__ __device__ constexpr int dot_mul_min_blocks(int R) { return R <= 8 ? 6 : 1; }
 
-#define DOT_S_(x) #x
-#define DOT_S(x) DOT_S_(x)
-#define MLO(d, a, w) "mad.lo.cc.u32 %" DOT_S(d) ", %" DOT_S(a) ", %" DOT_S(w) ", %" DOT_S(d) ";\n\t"
-#define MCLO(d, a, w) "madc.lo.cc.u32 %" DOT_S(d) ", %" DOT_S(a) ", %" DOT_S(w) ", %" DOT_S(d) ";\n\t"
-#define MCHI(d, a, w) "madc.hi.cc.u32 %" DOT_S(d) ", %" DOT_S(a) ", %" DOT_S(w) ", %" DOT_S(d) ";\n\t"
-
-// W[0..R+2) += a * (w_0 + w_1 X + ... + w_{R-1} X^{R-1})
+// Column sums of one block of R columns, kept as three 32-bit words each:
+// S_k = s2[k] X^2 + s1[k] X + s0[k]  (S_k < m 2^64 needs 64 + log2 m bits).
+// One partial product a * w_k is formed independently (Alg. 2 Phase 2: its low
+// and high halves) and added into column k with one carry chain of three words
+// (Phases 3-4 for that column).  Per product: 2 multiplies on the FMA pipe and
+// 3 adds on the integer ALU pipe, which run side by side.
 template <int R>
-__device__ __forceinline__ void mac_row(uint32_t (&W)[R + 2], uint32_t a, const uint32_t (&w)[R]);
-
-template <>
-__device__ __forceinline__ void mac_row<4>(uint32_t (&W)[6], uint32_t a, const uint32_t (&w)[4])
+__device__ __forceinline__ void mac_cols(uint32_t (&s0)[R], uint32_t (&s1)[R], uint32_t (&s2)[R], uint32_t a,
+                                         const uint32_t (&w)[R])
 {
-    // even products: words (0,1), (2,3); then carry into 4, 5
-    asm(MLO(0, 6, 7) MCHI(1, 6, 7) MCLO(2, 6, 8) MCHI(3, 6, 8)
-        "addc.cc.u32 %4, %4, 0;\n\t"
-        "addc.u32 %5, %5, 0;"
-        : "+r"(W[0]), "+r"(W[1]), "+r"(W[2]), "+r"(W[3]), "+r"(W[4]), "+r"(W[5])
-        : "r"(a), "r"(w[0]), "r"(w[2]));
-    // odd products: words (1,2), (3,4); then carry into 5
-    asm(MLO(0, 5, 6) MCHI(1, 5, 6) MCLO(2, 5, 7) MCHI(3, 5, 7)
-        "addc.u32 %4, %4, 0;"
-        : "+r"(W[1]), "+r"(W[2]), "+r"(W[3]), "+r"(W[4]), "+r"(W[5])
-        : "r"(a), "r"(w[1]), "r"(w[3]));
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+        asm("{\n\t.reg .u32 lo, hi;\n\t"
+            "mul.lo.u32 lo, %3, %4;\n\t"
+            "mul.hi.u32 hi, %3, %4;\n\t"
+            "add.cc.u32 %0, %0, lo;\n\t"
+            "addc.cc.u32 %1, %1, hi;\n\t"
+            "addc.u32 %2, %2, 0;\n\t}"
+            : "+r"(s0[k]), "+r"(s1[k]), "+r"(s2[k])
+            : "r"(a), "r"(w[k]));
 }
 
-template <>
-__device__ __forceinline__ void mac_row<8>(uint32_t (&W)[10], uint32_t a, const uint32_t (&w)[8])
+// Positional value of the block, W = sum_k S_k X^k, as R + 2 words.  The sum
+// is below m X^(R+1) (1 + 1/X), so R + 2 words always hold it.
+template <int R>
+__device__ __forceinline__ void cols_to_positional(const uint32_t (&s0)[R], const uint32_t (&s1)[R],
+                                                   const uint32_t (&s2)[R], uint32_t (&W)[R + 2])
 {
-    asm(MLO(0, 10, 11) MCHI(1, 10, 11) MCLO(2, 10, 12) MCHI(3, 10, 12)
-        MCLO(4, 10, 13) MCHI(5, 10, 13) MCLO(6, 10, 14) MCHI(7, 10, 14)
-        "addc.cc.u32 %8, %8, 0;\n\t"
-        "addc.u32 %9, %9, 0;"
-        : "+r"(W[0]), "+r"(W[1]), "+r"(W[2]), "+r"(W[3]), "+r"(W[4]), "+r"(W[5]), "+r"(W[6]),
-          "+r"(W[7]), "+r"(W[8]), "+r"(W[9])
-        : "r"(a), "r"(w[0]), "r"(w[2]), "r"(w[4]), "r"(w[6]));
-    asm(MLO(0, 9, 10) MCHI(1, 9, 10) MCLO(2, 9, 11) MCHI(3, 9, 11)
-        MCLO(4, 9, 12) MCHI(5, 9, 12) MCLO(6, 9, 13) MCHI(7, 9, 13)
-        "addc.u32 %8, %8, 0;"
-        : "+r"(W[1]), "+r"(W[2]), "+r"(W[3]), "+r"(W[4]), "+r"(W[5]), "+r"(W[6]), "+r"(W[7]),
-          "+r"(W[8]), "+r"(W[9])
-        : "r"(a), "r"(w[1]), "r"(w[3]), "r"(w[5]), "r"(w[7]));
-}
-
-template <>
-__device__ __forceinline__ void mac_row<16>(uint32_t (&W)[18], uint32_t a, const uint32_t (&w)[16])
-{
-    asm(MLO(0, 18, 19) MCHI(1, 18, 19) MCLO(2, 18, 20) MCHI(3, 18, 20)
-        MCLO(4, 18, 21) MCHI(5, 18, 21) MCLO(6, 18, 22) MCHI(7, 18, 22)
-        MCLO(8, 18, 23) MCHI(9, 18, 23) MCLO(10, 18, 24) MCHI(11, 18, 24)
-        MCLO(12, 18, 25) MCHI(13, 18, 25) MCLO(14, 18, 26) MCHI(15, 18, 26)
-        "addc.cc.u32 %16, %16, 0;\n\t"
-        "addc.u32 %17, %17, 0;"
-        : "+r"(W[0]), "+r"(W[1]), "+r"(W[2]), "+r"(W[3]), "+r"(W[4]), "+r"(W[5]), "+r"(W[6]),
-          "+r"(W[7]), "+r"(W[8]), "+r"(W[9]), "+r"(W[10]), "+r"(W[11]), "+r"(W[12]),
-          "+r"(W[13]), "+r"(W[14]), "+r"(W[15]), "+r"(W[16]), "+r"(W[17])
-        : "r"(a), "r"(w[0]), "r"(w[2]), "r"(w[4]), "r"(w[6]), "r"(w[8]), "r"(w[10]), "r"(w[12]),
-          "r"(w[14]));
-    asm(MLO(0, 17, 18) MCHI(1, 17, 18) MCLO(2, 17, 19) MCHI(3, 17, 19)
-        MCLO(4, 17, 20) MCHI(5, 17, 20) MCLO(6, 17, 21) MCHI(7, 17, 21)
-        MCLO(8, 17, 22) MCHI(9, 17, 22) MCLO(10, 17, 23) MCHI(11, 17, 23)
-        MCLO(12, 17, 24) MCHI(13, 17, 24) MCLO(14, 17, 25) MCHI(15, 17, 25)
-        "addc.u32 %16, %16, 0;"
-        : "+r"(W[1]), "+r"(W[2]), "+r"(W[3]), "+r"(W[4]), "+r"(W[5]), "+r"(W[6]), "+r"(W[7]),
-          "+r"(W[8]), "+r"(W[9]), "+r"(W[10]), "+r"(W[11]), "+r"(W[12]), "+r"(W[13]),
-          "+r"(W[14]), "+r"(W[15]), "+r"(W[16]), "+r"(W[17])
-        : "r"(a), "r"(w[1]), "r"(w[3]), "r"(w[5]), "r"(w[7]), "r"(w[9]), "r"(w[11]), "r"(w[13]),
-          "r"(w[15]));
+    uint64_t c = 0;
+#pragma unroll
+    for (int j = 0; j < R + 2; ++j) {
+        uint64_t t = c;
+        if (j < R) t += s0[j];
+        if (j >= 1 && j - 1 < R) t += s1[j - 1];
+        if (j >= 2) t += s2[j - 2];
+        W[j] = (uint32_t)t;
+        c = t >> 32;
+    }
 }
 
 template <int R>
@@ -88,37 +62,34 @@ __device__ __forceinline__ void lds_vec(const uint32_t *p, uint32_t *v)
 
 // Positional sum W = sum_{k<R} S_{c0+k} X^k of the block of columns [c0, c0+R),
 // S_c = sum_{i+j=c} A_i B_j.  As = A[0..m'), Bs = B[-R .. m'+R) (zeros outside
-// [0, m)), both in shared memory.  Rows i are taken R at a time; the needed
-// B values form a window that slides down by R per group.
+// [0, m)), both in shared memory.  For row i the block needs B[c0 + k - i],
+// k < R: a window of R values that slides down by one per row, so each row
+// reads A_i (a broadcast) and one new B value; rows are unrolled R at a time
+// so the slide is register renaming.
 template <int R>
 __device__ __forceinline__ void colsum_block(const uint32_t *As, const uint32_t *Bs, int c0, int mp,
                                              uint32_t (&W)[R + 2])
 {
+    uint32_t s0[R], s1[R], s2[R];
 #pragma unroll
-    for (int k = 0; k < R + 2; ++k) W[k] = 0;
+    for (int k = 0; k < R; ++k) s0[k] = s1[k] = s2[k] = 0;
     const int i_lo = max(0, c0 - mp + 1);
     const int i_hi = min(c0 + R - 1, mp - 1);
     int i0 = (i_lo / R) * R;
-    if (i0 > i_hi) return;
-    uint32_t bw[2 * R];
-    // window bw[q] = B[c0 - i0 - R + q]
-    lds_vec<2 * R>(Bs + R + (c0 - i0 - R), bw);
-    for (;;) {
-        uint32_t av[R];
-        lds_vec<R>(As + i0, av);
+    if (i0 <= i_hi) {
+        uint32_t w[R];
+        lds_vec<R>(Bs + R + (c0 - i0), w);   // w[k] = B[c0 + k - i0]
+        for (; i0 <= i_hi; i0 += R) {
 #pragma unroll
-        for (int ii = 0; ii < R; ++ii) {
-            uint32_t w[R];
+            for (int ii = 0; ii < R; ++ii) {
+                mac_cols<R>(s0, s1, s2, As[i0 + ii], w);
 #pragma unroll
-            for (int k = 0; k < R; ++k) w[k] = bw[R + k - ii];
-            mac_row<R>(W, av[ii], w);
+                for (int k = R - 1; k > 0; --k) w[k] = w[k - 1];
+                w[0] = Bs[R + c0 - (i0 + ii) - 1];
+            }
         }
-        i0 += R;
-        if (i0 > i_hi) break;
-#pragma unroll
-        for (int q = 0; q < R; ++q) bw[R + q] = bw[q];
-        lds_vec<R>(Bs + R + (c0 - i0 - R), bw);
     }
+    cols_to_positional<R>(s0, s1, s2, W);
 }
 
 // Copy limbs [t R, t R + R) of an m-limb row into shared memory (zeros past m).
@@ -153,7 +124,9 @@ __device__ __forceinline__ void store_block(uint32_t *row, int pos, int len, con
 // One op on a run of T lanes (lane t of the run, grp-th run of the warp), of
 // which the first tn = mp / R hold column blocks.  Every lane of the warp must
 // call this (it uses warp collectives); lanes with on == false or t >= tn take
-// part without touching memory.
+// part without touching memory.  The low half of the product is resolved and
+// stored before the high blocks are summed, so only its carry-out and the two
+// overflow words of the top low block are kept across.
 template <int R>
 __device__ __forceinline__ void mul_group(const uint32_t *As, const uint32_t *Bs, int t, int T,
                                           int tn, int grp, bool on, int m, int mp, uint32_t *prow,
@@ -161,42 +134,58 @@ __device__ __forceinline__ void mul_group(const uint32_t *As, const uint32_t *Bs
 {
     const int lane = (int)lane_id();
     on = on && t < tn;
-    uint32_t W0[R + 2], W1[R + 2];
-    if (on) {
-        colsum_block<R>(As, Bs, t * R, mp, W0);
-        colsum_block<R>(As, Bs, mp + t * R, mp, W1);
-    } else {
-#pragma unroll
-        for (int k = 0; k < R + 2; ++k) W0[k] = W1[k] = 0;
-    }
-    // overflow words of each block move to the next block in position order
     const int last = min(grp * T + max(tn, 1) - 1, 31);
-    const uint32_t u0l = __shfl_up_sync(DOT_FULL, W0[R], 1), u0h = __shfl_up_sync(DOT_FULL, W0[R + 1], 1);
-    const uint32_t u1l = __shfl_up_sync(DOT_FULL, W1[R], 1), u1h = __shfl_up_sync(DOT_FULL, W1[R + 1], 1);
-    const uint32_t wl = __shfl_sync(DOT_FULL, W0[R], last), wh = __shfl_sync(DOT_FULL, W0[R + 1], last);
-    uint32_t h0[R], h1[R], l0[R], l1[R];
+    uint32_t W[R + 2];
+    uint32_t wl, wh, mid;
+    {   // low blocks [tR, tR + R): positions 0 .. m' - 1
+        if (on) {
+            colsum_block<R>(As, Bs, t * R, mp, W);
+        } else {
 #pragma unroll
-    for (int k = 0; k < R; ++k) {
-        h0[k] = h1[k] = 0;
-        l0[k] = W0[k];
-        l1[k] = W1[k];
+            for (int k = 0; k < R + 2; ++k) W[k] = 0;
+        }
+        // the two overflow words of each block belong to the next block
+        const uint32_t ul = __shfl_up_sync(DOT_FULL, W[R], 1), uh = __shfl_up_sync(DOT_FULL, W[R + 1], 1);
+        wl = __shfl_sync(DOT_FULL, W[R], last);   // top low block -> first high block
+        wh = __shfl_sync(DOT_FULL, W[R + 1], last);
+        uint32_t l[R], h[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            l[k] = W[k];
+            h[k] = 0;
+        }
+        h[0] = t ? ul : 0u;
+        h[1] = t ? uh : 0u;
+        Segment<false, R> sg;
+        sg.phase12(l, h);
+        WarpCarry wc;
+        wc.resolve(on ? sg.g() : 0u, on ? sg.p() : 0u, 0u, smask, tmask);
+        mid = wc.carry_out(last);   // carry from the low half into the high half
+        sg.apply(wc.carry_in(lane));
+        if (on) store_block<R>(prow, t * R, 2 * m, sg.r, vec_out);
     }
-    h0[0] = t ? u0l : 0u;
-    h0[1] = t ? u0h : 0u;
-    h1[0] = t ? u1l : wl;
-    h1[1] = t ? u1h : wh;
-    Segment<false, R> s0, s1;
-    s0.phase12(l0, h0);
-    s1.phase12(l1, h1);
-    WarpCarry c0, c1;
-    c0.resolve(on ? s0.g() : 0u, on ? s0.p() : 0u, 0u, smask, tmask);
-    const uint32_t mid = c0.carry_out(last);   // carry from the low half into the high half
-    c1.resolve(on ? s1.g() : 0u, on ? s1.p() : 0u, t == 0 ? mid : 0u, smask, tmask);
-    s0.apply(c0.carry_in(lane));
-    s1.apply(c1.carry_in(lane));
-    if (on) {
-        store_block<R>(prow, t * R, 2 * m, s0.r, vec_out);
-        store_block<R>(prow, mp + t * R, 2 * m, s1.r, vec_out);
+    {   // high blocks [m' + tR, m' + tR + R)
+        if (on) {
+            colsum_block<R>(As, Bs, mp + t * R, mp, W);
+        } else {
+#pragma unroll
+            for (int k = 0; k < R + 2; ++k) W[k] = 0;
+        }
+        const uint32_t ul = __shfl_up_sync(DOT_FULL, W[R], 1), uh = __shfl_up_sync(DOT_FULL, W[R + 1], 1);
+        uint32_t l[R], h[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            l[k] = W[k];
+            h[k] = 0;
+        }
+        h[0] = t ? ul : wl;
+        h[1] = t ? uh : wh;
+        Segment<false, R> sg;
+        sg.phase12(l, h);
+        WarpCarry wc;
+        wc.resolve(on ? sg.g() : 0u, on ? sg.p() : 0u, t == 0 ? mid : 0u, smask, tmask);
+        sg.apply(wc.carry_in(lane));
+        if (on) store_block<R>(prow, mp + t * R, 2 * m, sg.r, vec_out);
     }
 }
 
