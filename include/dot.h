@@ -177,6 +177,29 @@ DOT_API dot_status_t dot_sub_host(dot_ctx_t ctx, const uint32_t *a, const uint32
 DOT_API dot_status_t dot_mul_host(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b,
                                   uint32_t *p, size_t m, size_t batch, dot_stream_t stream);
 
+/* ------------------------------------------------------------ autotuning --- */
+
+/* Tile and limbs-per-thread shapes, chosen per context and per size class
+ * (op, bit length of m).  The paper fixes its SIMD width at compile time;
+ * this table and the autotuner are this library's own.  A knob value is:
+ *   DOT_OP_MUL: R, the output columns each thread accumulates (4, 8 or 16;
+ *               needs m <= 32 R);
+ *   DOT_OP_ADD / DOT_OP_SUB: segments per thread of the tiled look-back
+ *               kernel (1, 2 or 4, i.e. 1024- to 4096-limb tiles; used only
+ *               for operands longer than 512 limbs).
+ * 0 restores the built-in choice.  Errors: DOT_EINVAL for an unknown op, m 0
+ * or a value the kernels do not implement for m. */
+DOT_API dot_status_t dot_tune_set(dot_ctx_t ctx, int op, size_t m, int value);
+DOT_API dot_status_t dot_tune_get(dot_ctx_t ctx, int op, size_t m, int *value);
+
+/* Time every valid knob for (op, m) on `batch` synthetic operand pairs
+ * (device memory allocated and freed inside the call; synchronous, on the
+ * ctx's private stream), keep the fastest in the table and return it in
+ * *best (and its mean time per call in *best_ms, which may be NULL).
+ * *best is 0 when the size has nothing to tune (add/sub of <= 512 limbs). */
+DOT_API dot_status_t dot_autotune(dot_ctx_t ctx, int op, size_t m, size_t batch, int *best,
+                                  float *best_ms);
+
 /* ------------------------------------------------- allocation-free add --- */
 
 /* dot_add without any device allocation, for callers that must not call

@@ -244,6 +244,151 @@ addsub_tile_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint32_t *
     }
 }
 
+// ============================ tiled kernel (2b): bulk-copy prefetch + look-back
+// Same tiles, tickets and look-back as above, for 16-byte aligned rows with
+// m % 4 == 0.  Each block keeps two tiles in flight: thread 0 takes the next
+// ticket as soon as the block has read the current tile out of shared memory
+// and starts that tile's operand copies (cp.async.bulk, completion counted on
+// an mbarrier), so HBM keeps streaming while the block waits in look-back.
+// A block processes its tickets in the order it took them, so the lowest
+// unfinished ticket always belongs to a block that is processing it (not
+// prefetching it) and whose predecessors are done: the waits still end.
+template <bool SUB, int NCH>
+__global__ void __launch_bounds__(DOT_TILE_THREADS)
+addsub_tile_bulk_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint32_t *cout,
+                        size_t m, size_t batch, unsigned long long tiles_per_op, LookbackArgs lb)
+{
+    constexpr int WARPS = DOT_TILE_THREADS / 32;
+    constexpr unsigned long long TILE = (unsigned long long)DOT_TILE_THREADS * 4 * NCH;
+    constexpr int WARP_LIMBS = 32 * 4 * NCH;
+    extern __shared__ __align__(128) uint32_t stage[];   // [2][2][TILE]: stage, operand
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ unsigned long long s_ticket[2];
+    __shared__ uint32_t s_wagg[2][WARPS];
+    __shared__ uint32_t s_cin[2];
+    const int lane = (int)lane_id();
+    const int warp = (int)(threadIdx.x >> 5);
+    const unsigned long long epoch = lb.counters[2];
+    const unsigned long long total = (unsigned long long)batch * tiles_per_op;
+
+    auto issue = [&](int st) {   // thread 0: take a ticket and start its copies
+        const unsigned long long tk = atomicAdd(&lb.counters[0], 1ull);
+        s_ticket[st] = tk;
+        if (tk < total) {
+            const unsigned long long op = tk / tiles_per_op, t = tk - op * tiles_per_op;
+            const size_t first = (size_t)(t * TILE);
+            const size_t lim = (m - first < TILE) ? m - first : (size_t)TILE;
+            const uint32_t bytes = (uint32_t)(lim * 4);
+            mbar_arrive_expect_tx(&s_bar[st], 2 * bytes);
+            bulk_g2s(stage + (2 * st) * TILE, a + op * m + first, bytes, &s_bar[st]);
+            bulk_g2s(stage + (2 * st + 1) * TILE, b + op * m + first, bytes, &s_bar[st]);
+        }
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        mbar_init_fence();
+        issue(0);
+        issue(1);
+    }
+    __syncthreads();
+
+    for (int k = 0;; ++k) {
+        const int st = k & 1;
+        const unsigned long long ticket = s_ticket[st];
+        if (ticket >= total) break;
+        const unsigned long long op = ticket / tiles_per_op;
+        const unsigned long long t = ticket - op * tiles_per_op;
+        const size_t wbase = (size_t)(t * TILE) + (size_t)warp * WARP_LIMBS;
+        if (!mbar_wait_bounded(&s_bar[st], (uint32_t)((k >> 1) & 1), lb.wait_limit_ns) && lane == 0)
+            record_status(lb.status, DOT_ETIMEOUT);
+        const uint32_t *xa = stage + (2 * st) * TILE + warp * WARP_LIMBS;
+        const uint32_t *xb = stage + (2 * st + 1) * TILE + warp * WARP_LIMBS;
+        uint32_t x[NCH][4], y[NCH][4];
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) {
+            const size_t li = wbase + ((size_t)j * 32 + lane) * 4;
+            if (li < m) {
+                const uint4 qa = reinterpret_cast<const uint4 *>(xa)[j * 32 + lane];
+                const uint4 qb = reinterpret_cast<const uint4 *>(xb)[j * 32 + lane];
+                x[j][0] = qa.x; x[j][1] = qa.y; x[j][2] = qa.z; x[j][3] = qa.w;
+                y[j][0] = qb.x; y[j][1] = qb.y; y[j][2] = qb.z; y[j][3] = qb.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) x[j][i] = y[j][i] = 0;
+            }
+        }
+        Segment<SUB, 4> sg[NCH];
+        uint32_t G[NCH], P[NCH];
+        uint32_t wg = 0, wp = 1;
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) {
+            sg[j].phase12(x[j], y[j]);
+            const size_t li = wbase + ((size_t)j * 32 + lane) * 4;
+            const bool on = li < m;
+            WarpCarry wc;
+            wc.resolve(on ? sg[j].g() : 0u, on ? sg[j].p() : 0u, 0u, 1u, 0x80000000u);
+            G[j] = wc.G;
+            P[j] = wc.P;
+            gp_compose(wg, wp, wc.carry_out(31), (uint32_t)(wc.P == DOT_FULL));
+        }
+        if (lane == 0) s_wagg[st][warp] = wg | (wp << 1);
+        __syncthreads();   // stage st fully read; warp aggregates visible
+        if (threadIdx.x == 0) issue(st);
+
+        if (warp == 0) {
+            uint32_t tg = 0, tp = 1;
+#pragma unroll
+            for (int w = 0; w < WARPS; ++w) gp_compose(tg, tp, s_wagg[st][w] & 1u, s_wagg[st][w] >> 1);
+            unsigned long long *st_op = lb.state + (ticket - t);
+            const bool skip = lb.skip_tile >= 0 && op == 0 && (long long)t == lb.skip_tile;
+            uint32_t cin_tile = 0;
+            if (t == 0) {
+                if (lane == 0 && !skip)
+                    st_release_u64(st_op, (epoch << 2) | (tg ? LB_INCL1 : LB_INCL0));
+            } else {
+                if (lane == 0 && !skip)
+                    st_release_u64(st_op + t, (epoch << 2) | (tp ? LB_PROP : (tg ? LB_INCL1 : LB_INCL0)));
+                cin_tile = lookback_carry(lb, st_op, (long long)t, epoch, lane);
+                if (tp && lane == 0 && !skip)
+                    st_release_u64(st_op + t, (epoch << 2) | (cin_tile ? LB_INCL1 : LB_INCL0));
+            }
+            if (lane == 0) s_cin[st] = cin_tile;
+        }
+        __syncthreads();
+
+        uint32_t c = s_cin[st];
+        for (int w = 0; w < warp; ++w) {
+            const uint32_t g = s_wagg[st][w] & 1u, p = s_wagg[st][w] >> 1;
+            c = g | (p & c);
+        }
+        uint32_t *sr = s + op * m;
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) {
+            const size_t li = wbase + ((size_t)j * 32 + lane) * 4;
+            const uint32_t Pm = P[j] & 0x7fffffffu;
+            const uint32_t C = (((G[j] << 1) | c) + Pm) ^ Pm;
+            const uint32_t ci = (C >> lane) & 1u;
+            sg[j].apply(ci);
+            if (li < m) {
+                store_seg<4>(sr + li, sg[j].r);
+                if (li + 4 >= m && t == tiles_per_op - 1) cout[op] = sg[j].cout(ci);
+            }
+            c = ((G[j] >> 31) | ((P[j] >> 31) & (C >> 31))) & 1u;
+        }
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned long long prev = atomicAdd(&lb.counters[1], 1ull);
+        if (prev == gridDim.x - 1) {
+            lb.counters[0] = 0;
+            lb.counters[1] = 0;
+            __threadfence();
+            lb.counters[2] = epoch + 1;
+        }
+    }
+}
+
 // ===================================================== ragged kernel (one warp per op)
 template <bool SUB>
 __global__ void __launch_bounds__(WARP_KERNEL_THREADS)
@@ -301,13 +446,31 @@ static dot_status_t launch_tile(dot_ctx_t ctx, const dot_plan_t &pl, const uint3
     dot_status_t rc = dot_lookback_prepare(ctx, tiles, &lb);
     if (rc != DOT_OK) return rc;
     ctx->debug_skip_tile = -1;   // the hook fires once
+    const unsigned long long tpo = pl.tiles;
+    if constexpr (SEG == 4) {
+        // 16-byte aligned rows: the kernel with bulk-copy prefetch
+        const size_t smem = (size_t)2 * 2 * DOT_TILE_THREADS * 4 * pl.chunks * 4;
+        const void *fb = pl.chunks == 1 ? (const void *)addsub_tile_bulk_kernel<SUB, 1>
+                       : pl.chunks == 2 ? (const void *)addsub_tile_bulk_kernel<SUB, 2>
+                                        : (const void *)addsub_tile_bulk_kernel<SUB, 4>;
+        if (cudaFuncSetAttribute(fb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return DOT_ECUDA;
+        const size_t cap = (size_t)ctx->num_sms * dot_blocks_per_sm(fb, DOT_TILE_THREADS, smem);
+        const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
+        if (pl.chunks == 1)
+            addsub_tile_bulk_kernel<SUB, 1><<<grid, DOT_TILE_THREADS, smem, st>>>(a, b, s, cout, m, batch, tpo, lb);
+        else if (pl.chunks == 2)
+            addsub_tile_bulk_kernel<SUB, 2><<<grid, DOT_TILE_THREADS, smem, st>>>(a, b, s, cout, m, batch, tpo, lb);
+        else
+            addsub_tile_bulk_kernel<SUB, 4><<<grid, DOT_TILE_THREADS, smem, st>>>(a, b, s, cout, m, batch, tpo, lb);
+        return cudaGetLastError() == cudaSuccess ? DOT_OK : DOT_ECUDA;
+    }
     const void *fn;
     if (pl.chunks == 1) fn = (const void *)addsub_tile_kernel<SUB, SEG, 1>;
     else if (pl.chunks == 2) fn = (const void *)addsub_tile_kernel<SUB, SEG, 2>;
     else fn = (const void *)addsub_tile_kernel<SUB, SEG, 4>;
     const size_t cap = (size_t)ctx->num_sms * dot_blocks_per_sm(fn, DOT_TILE_THREADS, 0);
     const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
-    const unsigned long long tpo = pl.tiles;
     if (pl.chunks == 1)
         addsub_tile_kernel<SUB, SEG, 1><<<grid, DOT_TILE_THREADS, 0, st>>>(a, b, s, cout, m, batch, tpo, lb);
     else if (pl.chunks == 2)
@@ -335,7 +498,8 @@ static dot_status_t addsub_batched(dot_ctx_t ctx, const uint32_t *a, const uint3
     if (m == 0) return cudaMemsetAsync(cout, 0, batch * 4, st) == cudaSuccess ? DOT_OK : DOT_ECUDA;
     const bool vec = (m % 4 == 0) && aligned16(a) && aligned16(b) && aligned16(s);
     dot_plan_t pl;
-    rc = dot_make_plan(SUB ? DOT_OP_SUB : DOT_OP_ADD, m, batch, vec, &pl);
+    const int op = SUB ? DOT_OP_SUB : DOT_OP_ADD;
+    rc = dot_make_plan(op, m, batch, vec, &pl, ctx->tune[op][dot_tune_bucket(m)]);
     if (rc != DOT_OK) return rc;
     if (pl.kernel == DOT_K_ADDSUB_WARP) {
         cudaError_t e = vec ? launch_warp<SUB, 4>(ctx, pl, a, b, s, cout, m, batch, st)

@@ -165,7 +165,7 @@ DOT_API dot_status_t dot_mul(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b
     const size_t in = m * batch * 4, out = 2 * in;
     if (any_overlap(p, out, a, in) || any_overlap(p, out, b, in)) return DOT_EINVAL;
     dot_plan_t pl;
-    rc = dot_make_plan(DOT_OP_MUL, m, batch, true, &pl);
+    rc = dot_make_plan(DOT_OP_MUL, m, batch, true, &pl, ctx->tune[DOT_OP_MUL][dot_tune_bucket(m)]);
     if (rc != DOT_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     switch (pl.seg_limbs) {

@@ -26,7 +26,29 @@ static inline int dot_mul_cols(size_t m)
     return m <= 16 ? 4 : (m <= 256 ? 8 : 16);
 }
 
-static inline dot_status_t dot_make_plan(int op, size_t m, size_t batch, bool vec, dot_plan_t *pl)
+// Size bucket of the tuning table: the bit length of m (m in [2^(b-1), 2^b)).
+#define DOT_TUNE_BUCKETS 65
+static inline int dot_tune_bucket(size_t m)
+{
+    int b = 0;
+    while (m) {
+        ++b;
+        m >>= 1;
+    }
+    return b;
+}
+
+// Whether `knob` is a shape the kernels implement for (op, m):
+//   mul    -- R, the columns per block: 4, 8 or 16 with m <= 32 R;
+//   add/sub -- segments per thread of the tiled look-back kernel: 1, 2 or 4.
+static inline bool dot_knob_valid(int op, size_t m, int knob)
+{
+    if (op == DOT_OP_MUL) return (knob == 4 || knob == 8 || knob == 16) && m <= (size_t)32 * knob;
+    return knob == 1 || knob == 2 || knob == 4;
+}
+
+// knob: a tuned shape (see dot_knob_valid), or 0 for the built-in choice.
+static inline dot_status_t dot_make_plan(int op, size_t m, size_t batch, bool vec, dot_plan_t *pl, int knob = 0)
 {
     pl->kernel = DOT_K_NONE;
     pl->seg_limbs = 1;
@@ -40,7 +62,7 @@ static inline dot_status_t dot_make_plan(int op, size_t m, size_t batch, bool ve
     if (op == DOT_OP_MUL) {
         if (m == 0) return DOT_OK;
         if (m > DOT_MUL_MAX_LIMBS) return DOT_EUNSUPPORTED;
-        const int R = dot_mul_cols(m);
+        const int R = (knob && dot_knob_valid(op, m, knob)) ? knob : dot_mul_cols(m);
         pl->kernel = DOT_K_MUL_COLSUM;
         pl->seg_limbs = R;
         pl->m_pad = dot_ceil_div(m, (size_t)R) * R;
@@ -73,7 +95,7 @@ static inline dot_status_t dot_make_plan(int op, size_t m, size_t batch, bool ve
     pl->lanes_per_op = DOT_TILE_THREADS;
     // segments per thread: 4 for long operands, fewer for short ones
     const size_t per4 = (size_t)DOT_TILE_THREADS * seg * 4;
-    pl->chunks = m >= per4 ? 4 : (m >= per4 / 2 ? 2 : 1);
+    pl->chunks = (knob && dot_knob_valid(op, m, knob)) ? knob : (m >= per4 ? 4 : (m >= per4 / 2 ? 2 : 1));
     pl->tile_limbs = (uint64_t)DOT_TILE_THREADS * seg * pl->chunks;
     pl->tiles = dot_ceil_div(m, (size_t)pl->tile_limbs);
     return DOT_OK;

@@ -72,6 +72,10 @@ _SIGS = {
     "dot_sub_host": (_st, [_vp, _vp, _vp, _vp, _vp, _sz, _sz, _vp]),
     "dot_mul_host": (_st, [_vp, _vp, _vp, _vp, _sz, _sz, _vp]),
     "dot_add_noalloc": (_st, [ctypes.c_int, _vp, _vp, _vp, _vp, _sz, _sz, _vp]),
+    "dot_tune_set": (_st, [_vp, ctypes.c_int, _sz, ctypes.c_int]),
+    "dot_tune_get": (_st, [_vp, ctypes.c_int, _sz, ctypes.POINTER(ctypes.c_int)]),
+    "dot_autotune": (_st, [_vp, ctypes.c_int, _sz, _sz, ctypes.POINTER(ctypes.c_int),
+                           ctypes.POINTER(ctypes.c_float)]),
 }
 
 _lib = None
@@ -154,6 +158,22 @@ class Context:
 
     def debug_skip_publish(self, tile: int):
         _chk(lib().dot_debug_skip_publish(self.handle, int(tile)), "dot_debug_skip_publish")
+
+    def tune_set(self, op: int, m: int, value: int):
+        _chk(lib().dot_tune_set(self.handle, op, m, value), "dot_tune_set")
+
+    def tune_get(self, op: int, m: int) -> int:
+        v = ctypes.c_int()
+        _chk(lib().dot_tune_get(self.handle, op, m, ctypes.byref(v)), "dot_tune_get")
+        return v.value
+
+    def autotune(self, op: int, m: int, batch: int):
+        """Time the candidate shapes for (op, m) and keep the fastest in this
+        context; returns (knob, ms per call)."""
+        best, ms = ctypes.c_int(), ctypes.c_float()
+        _chk(lib().dot_autotune(self.handle, op, m, batch, ctypes.byref(best), ctypes.byref(ms)),
+             "dot_autotune")
+        return best.value, ms.value
 
 
 _default_ctx = {}
