@@ -410,12 +410,24 @@ def profile_case(args):
     """Small cases for ncu, a few launches each:
     add  -- dot_add on 2^18 pairs of 4096-bit operands (403 MB, > L2);
     long -- dot_add on 16 pairs of 2^22-bit operands (25 MB, look-back tiles);
-    mul  -- dot_mul on 2^16 pairs of 8192-bit operands (256 MB in + out)."""
+    mul  -- dot_mul on 2^16 pairs of 8192-bit operands (256 MB in + out);
+    shared -- dot_mul_shared on the tensor cores, 2^16 x 2048-bit (50 MB)."""
     import torch
     from paper_2604_21566_gb300 import dot
     from paper_2604_21566_gb300 import workloads as W
     torch.cuda.set_device(0)
     ctx = dot.Context(0)
+    if args.case == "shared":
+        f, bb = W.shared_operand()
+        fd = torch.from_numpy(f.view(np.int32)).cuda()
+        b = torch.from_numpy(bb.view(np.int32)).cuda()
+        p = torch.empty((bb.shape[0], 128), dtype=torch.int32, device="cuda")
+        for _ in range(args.launches):
+            dot.mul_shared(fd, b, p, tensor_cores=True, ctx=ctx)
+        torch.cuda.synchronize()
+        assert ctx.check() == dot.OK
+        print("profile case done")
+        return
     if args.case == "mul":
         x, y, _ = W.batched_mul(256)
     elif args.case == "long":
@@ -586,16 +598,37 @@ def suite(args):
                            "peak": peak, "frac": round(2.0 * prods / (t_mixed * 1e-3) / peak, 4)}})
 
     if want("shared"):
-        # -- shared operand: INT32 column-sum path
+        # -- shared operand: Toeplitz product on the tensor cores vs the INT32 paths
         f, bb = W.shared_operand()
+        n = bb.shape[0]
         a = dv(np.ascontiguousarray(np.broadcast_to(f, bb.shape)))
-        b = dv(bb)
-        p = torch.empty((bb.shape[0], 128), dtype=torch.int32, device="cuda")
+        fd, b = dv(f), dv(bb)
+        p = torch.empty((n, 128), dtype=torch.int32, device="cuda")
+        sel = np.arange(0, n, 97)
+        want = oracle.mul(np.broadcast_to(f, (sel.size, 64)), bb[sel])
         t_int = _event_ms(lambda: dot.mul(a, b, p, ctx=ctx), 50, stream)
-        sel = np.arange(0, bb.shape[0], 97)
-        ok = np.array_equal(hs(p)[sel], oracle.mul(np.broadcast_to(f, (sel.size, 64)), bb[sel]))
+        ok = np.array_equal(hs(p)[sel], want)
+        t_int_sh = _event_ms(lambda: dot.mul_shared(fd, b, p, tensor_cores=False, ctx=ctx), 50, stream)
+        ok &= np.array_equal(hs(p)[sel], want)
+        t_tc = _event_ms(lambda: dot.mul_shared(fd, b, p, tensor_cores=True, ctx=ctx), 50, stream)
+        ok &= np.array_equal(hs(p)[sel], want)
+        # tensor work issued: 48 MMAs of 128 x 128 x 16 per 128 operands
+        flops = 2.0 * 128 * 128 * 16 * 48 * ((n + 127) // 128)
+        useful = 2.0 * 256 * 256 * n
+        hbm, _ = peaks()
+        tc_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"] \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
+        bytes_moved = n * (256 + 512) + 256
         emit({"workload": "shared operand: fixed 2048-bit x 2^16 2048-bit", "bit_exact_sample": bool(ok),
-              "ms_int32": round(t_int, 4), "gop_s_int32": round(bb.shape[0] / (t_int * 1e-3) / 1e9, 4)})
+              "ms_int32_batched": round(t_int, 4), "ms_int32_shared": round(t_int_sh, 4),
+              "ms_tensor": round(t_tc, 4), "speedup_tensor_vs_int32": round(t_int / t_tc, 3),
+              "gop_s_tensor": round(n / (t_tc * 1e-3) / 1e9, 4),
+              "roofline_tensor": {"issued_tflop_s": round(flops / (t_tc * 1e-3) / 1e12, 1),
+                                  "useful_tflop_s": round(useful / (t_tc * 1e-3) / 1e12, 1),
+                                  "peak_fp16_tflop_s": tc_peak,
+                                  "frac_issued": round(flops / (t_tc * 1e-3) / 1e12 / tc_peak, 4),
+                                  "GB_s": round(bytes_moved / (t_tc * 1e-3) / 1e9, 1),
+                                  "frac_hbm": round(bytes_moved / (t_tc * 1e-3) / 1e9 / hbm, 4)}})
     assert ctx.check() == dot.OK
     ctx.close()
 
@@ -608,7 +641,7 @@ def main():
                     help="run only the small ncu case of the dominant kernel")
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--only", default="", help="--suite rows to run: mix,mul,mixed,shared")
-    ap.add_argument("--case", choices=["add", "long", "mul"], default="add",
+    ap.add_argument("--case", choices=["add", "long", "mul", "shared"], default="add",
                     help="which kernel --profile-case runs")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)

@@ -136,6 +136,19 @@ DOT_API dot_status_t dot_mul_ragged(dot_ctx_t ctx, const uint32_t *a, const uint
                                     uint32_t *p, const uint64_t *off, const uint64_t *poff,
                                     size_t batch, dot_stream_t stream);
 
+/* One fixed operand times a batch: p[k] = fixed * b[k] as 2m limbs.
+ * fixed: uint32_t[m]; b: uint32_t[batch][m]; p: uint32_t[batch][2m] (no
+ * overlap with the inputs).  The column sums of Theorem 2 (Sec. 3.2) over
+ * 8-bit digits of a fixed operand form one matrix product with a Toeplitz
+ * matrix; use_tensor_cores != 0 runs it on the tensor cores (tcgen05.mma,
+ * fp16 digits, fp32 accumulation -- exact because every column sum is at
+ * most 256 * 255^2 < 2^24) and normalises the carries in the epilogue; it
+ * needs 1 <= m <= 64 (2048 bits), else DOT_EUNSUPPORTED.  use_tensor_cores
+ * == 0 runs the INT32 column-sum path of dot_mul (m <= DOT_MUL_MAX_LIMBS). */
+DOT_API dot_status_t dot_mul_shared(dot_ctx_t ctx, const uint32_t *fixed, const uint32_t *b,
+                                    uint32_t *p, size_t m, size_t batch, int use_tensor_cores,
+                                    dot_stream_t stream);
+
 /* ------------------------------------------------------------ mixed batch --- */
 
 /* One operation of a mixed ragged batch (32 bytes).  Operand a occupies

@@ -72,6 +72,7 @@ _SIGS = {
     "dot_sub_host": (_st, [_vp, _vp, _vp, _vp, _vp, _sz, _sz, _vp]),
     "dot_mul_host": (_st, [_vp, _vp, _vp, _vp, _sz, _sz, _vp]),
     "dot_add_noalloc": (_st, [ctypes.c_int, _vp, _vp, _vp, _vp, _sz, _sz, _vp]),
+    "dot_mul_shared": (_st, [_vp, _vp, _vp, _vp, _sz, _sz, ctypes.c_int, _vp]),
     "dot_tune_set": (_st, [_vp, ctypes.c_int, _sz, ctypes.c_int]),
     "dot_tune_get": (_st, [_vp, ctypes.c_int, _sz, ctypes.POINTER(ctypes.c_int)]),
     "dot_autotune": (_st, [_vp, ctypes.c_int, _sz, _sz, ctypes.POINTER(ctypes.c_int),
@@ -257,6 +258,23 @@ def mul(a, b, out=None, ctx=None, stream=None):
         raise ValueError("dot_mul: out must be [batch, 2m]")
     ctx = ctx or default_context(a.device.index)
     _chk(lib().dot_mul(ctx.handle, _ptr(a), _ptr(b), _ptr(out), m, batch, _stream(stream)), "dot_mul")
+    return out
+
+
+def mul_shared(fixed, b, out=None, tensor_cores=True, ctx=None, stream=None):
+    """p[k] = fixed * b[k] (2m limbs) for one fixed m-limb operand; on the
+    tensor cores (m <= 64) or on the INT32 column-sum path."""
+    import torch
+    _limb_tensor(fixed, "fixed"), _limb_tensor(b, "b")
+    if b.dim() != 2 or fixed.numel() != b.shape[1]:
+        raise ValueError("dot_mul_shared: fixed is [m], b is [batch, m]")
+    batch, m = b.shape
+    if out is None:
+        out = torch.empty((batch, 2 * m), dtype=b.dtype, device=b.device)
+    _limb_tensor(out, "out")
+    ctx = ctx or default_context(b.device.index)
+    _chk(lib().dot_mul_shared(ctx.handle, _ptr(fixed), _ptr(b), _ptr(out), m, batch, int(bool(tensor_cores)),
+                              _stream(stream)), "dot_mul_shared")
     return out
 
 

@@ -1,0 +1,86 @@
+"""Shared-operand products (one fixed operand x a batch) through the C ABI:
+the tensor-core Toeplitz path and the INT32 path, bit-exact vs the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import assert_same, dev, host
+from paper_2604_21566_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def D():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2604_21566_gb300 import dot
+    dot.lib()
+    return dot
+
+
+def run(D, f, b, tc):
+    import torch
+    p = D.mul_shared(dev(f), dev(b), tensor_cores=tc)
+    torch.cuda.synchronize()
+    return host(p)
+
+
+def want(f, b):
+    return oracle.mul(np.ascontiguousarray(np.broadcast_to(f, b.shape)), b, threads=8)
+
+
+@pytest.mark.parametrize("tc", [True, False])
+@pytest.mark.parametrize("m", [1, 2, 3, 7, 8, 31, 32, 33, 63, 64])
+@pytest.mark.parametrize("batch", [1, 127, 128, 129, 1000])
+def test_sizes(D, tc, m, batch):
+    g = W.rng(5000 + 13 * m + batch)
+    f = W.uniform_limbs(g, m)
+    b = W.uniform_limbs(g, (batch, m))
+    assert_same(run(D, f, b, tc), want(f, b), f"tc={tc} m={m} batch={batch}")
+
+
+@pytest.mark.parametrize("tc", [True, False])
+def test_largest_column_sums(D, tc):
+    """All-ones digits everywhere: every Toeplitz column sum reaches its bound
+    256 * 255^2 = 16,646,400 (just under 2^24); the result is (2^n - 1)^2."""
+    m = 64
+    f = np.full(m, 0xFFFFFFFF, np.uint32)
+    b = np.full((300, m), 0xFFFFFFFF, np.uint32)
+    p = run(D, f, b, tc)
+    wantrow = np.zeros(2 * m, np.uint32)
+    wantrow[0] = 1
+    wantrow[m] = 0xFFFFFFFE
+    wantrow[m + 1:] = 0xFFFFFFFF
+    assert_same(p, np.tile(wantrow, (300, 1)), f"tc={tc}")
+
+
+@pytest.mark.parametrize("tc", [True, False])
+def test_value_classes(D, tc):
+    g = W.rng(77)
+    for cls in W.CLASSES:
+        x, y = W.class_operands(g, cls, 257, 64)
+        f = x[0]
+        assert_same(run(D, f, y, tc), want(f, y), f"{cls} tc={tc}")
+
+
+def test_shared_operand_workload_full(D):
+    """The 2^16-operand, 2048-bit workload: tensor-core and INT32 paths agree
+    with each other on every row and with the oracle on every row."""
+    f, b = W.shared_operand()
+    p_tc = run(D, f, b, True)
+    p_int = run(D, f, b, False)
+    assert_same(p_tc, p_int, "tensor vs int32")
+    assert_same(p_tc, want(f, b), "tensor vs oracle")
+
+
+def test_limits(D):
+    import torch
+    f = torch.zeros(65, dtype=torch.int32, device="cuda")
+    b = torch.zeros((4, 65), dtype=torch.int32, device="cuda")
+    with pytest.raises(D.DotError) as e:
+        D.mul_shared(f, b, tensor_cores=True)
+    assert e.value.status == D.EUNSUPPORTED
+    D.mul_shared(f, b, tensor_cores=False)   # the INT32 path takes it
+    assert D.default_context().check() == D.OK
