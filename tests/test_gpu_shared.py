@@ -56,6 +56,31 @@ def test_largest_column_sums(D, tc):
     assert_same(p, np.tile(wantrow, (300, 1)), f"tc={tc}")
 
 
+FIXED_PATTERNS = {
+    "bytes_0x80": 0x80808080,      # balanced digits -128, then -127 each
+    "bytes_0x7f": 0x7F7F7F7F,
+    "alt_7f_80": 0x807F807F,       # balanced digits alternate near +-128
+    "alt_80_7f": 0x7F807F80,
+    "all_ones": 0xFFFFFFFF,        # every digit -1 with a carry, top digit +1
+    "top_bit": 0x80000000,
+}
+
+
+@pytest.mark.parametrize("tc", [True, False])
+@pytest.mark.parametrize("pattern", sorted(FIXED_PATTERNS))
+@pytest.mark.parametrize("m", [1, 5, 64])
+def test_digit_extremes(D, tc, pattern, m):
+    """Fixed operands whose balanced digits sit at +-128 and batch rows of all
+    zero digits (shifted to -128) or all 0xFF digits (127): the raw column sums
+    reach the ends of their range, and zero rows must give exact zeros."""
+    g = W.rng(900 + m)
+    f = np.full(m, FIXED_PATTERNS[pattern], np.uint32)
+    rows = [np.zeros(m, np.uint32), np.full(m, 0xFFFFFFFF, np.uint32), np.full(m, 0x80808080, np.uint32),
+            np.full(m, 0x7F7F7F7F, np.uint32)]
+    b = np.vstack(rows + [W.uniform_limbs(g, (200, m))])
+    assert_same(run(D, f, b, tc), want(f, b), f"{pattern} m={m} tc={tc}")
+
+
 @pytest.mark.parametrize("tc", [True, False])
 def test_value_classes(D, tc):
     g = W.rng(77)
