@@ -64,6 +64,12 @@ def bind(path: str):
     L.oracle_mixed.restype = ctypes.c_int
     L.oracle_vnc_pairs.argtypes = [_sz, _i32p, _i32p, _i32p]
     L.oracle_vnc_pairs.restype = ctypes.c_int
+    for name in ("oracle_add_gen", "oracle_sub_gen"):
+        f = getattr(L, name)
+        f.argtypes = [_u32p, _sz, _u32p, _sz, _u32p, _u32p, _u32p, _sz]
+        f.restype = ctypes.c_int
+    L.oracle_sqr.argtypes = [_u32p, _u32p, _sz, _sz]
+    L.oracle_sqr.restype = ctypes.c_int
     return L
 
 
@@ -128,6 +134,47 @@ def mul(a, b, threads: int = 1):
     B, m = a.shape
     p = np.empty((B, 2 * m), dtype=np.uint32)
     _run_rows(lib().oracle_mul, a, b, p, None, m, B, threads, out_limbs=2 * m)
+    return p
+
+
+def _gen(fn, what, a, b, cin):
+    a = _c(a)
+    b = _c(b)
+    if a.ndim == 1:
+        a, b = a[None, :], b[None, :]
+        cin = None if cin is None else np.atleast_1d(cin)
+    B, ma = a.shape
+    mb = b.shape[1]
+    if b.shape[0] != B:
+        raise ValueError("operand batches differ")
+    s = np.empty_like(a)
+    c = np.empty(B, dtype=np.uint32)
+    ci = None if cin is None else _c(cin)
+    if ci is not None and ci.size != B:
+        raise ValueError("carry-in must hold one word per row")
+    _check(fn(_p32(a), ma, _p32(b), mb, _p32(ci) if ci is not None else None, _p32(s), _p32(c), B), what)
+    return s, c
+
+
+def add_gen(a, b, cin=None):
+    """S, carry with S + carry X^ma = A + B + [cin != 0]; B ([batch][mb], mb <=
+    ma) padded with zeros; cin per row or None."""
+    return _gen(lib().oracle_add_gen, "oracle_add_gen", a, b, cin)
+
+
+def sub_gen(a, b, bin=None):
+    """D, borrow with D - borrow X^ma = A - B - [bin != 0]; B padded with zeros."""
+    return _gen(lib().oracle_sub_gen, "oracle_sub_gen", a, b, bin)
+
+
+def sqr(a):
+    """P = A * A as 2m limbs, row by row."""
+    a = _c(a)
+    if a.ndim == 1:
+        a = a[None, :]
+    B, m = a.shape
+    p = np.empty((B, 2 * m), dtype=np.uint32)
+    _check(lib().oracle_sqr(_p32(a), _p32(p), m, B), "oracle_sqr")
     return p
 
 

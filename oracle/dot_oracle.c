@@ -16,6 +16,11 @@
  *   add : S + c_out X^m = A + B                  (Theorem 1, Sec. 3.1)
  *   sub : D - b_out X^m = A - B, b_out in {0,1}  (Sec. 3.1, "Subtraction")
  *   mul : P = A * B as exactly 2m limbs          (Theorem 2, Sec. 3.2)
+ *   add_gen / sub_gen : the mpn-style variants (Sec. 3.3 and the textbook
+ *         MPN-ADD-M of the appendix): S + c X^ma = A + B + cin with B of
+ *         mb <= ma limbs padded with zeros (as in Theorem 2's proof), and
+ *         the borrow mirror D - b X^ma = A - B - bin
+ *   sqr : P = A * A as 2m limbs
  * The add/sub loops are the textbook S_i = A_i + B_i + C_{i-1} recurrence
  * (Sec. 2.2 and Alg. 3, MPN-ADD-M) with 64-bit intermediates; the product is
  * the ROW-wise schoolbook (operand scanning), deliberately not the column form
@@ -28,7 +33,8 @@
  *   - the product has exactly 2m limbs; Alg. 2's "prepend carry" branch is
  *     unreachable for A, B < X^m, so oracle_mul_vnc reports it as an error;
  *   - subtraction with A < B wraps modulo X^m and returns borrow 1;
- *   - there is no carry-in (Alg. 1 starts with c_out = 0).
+ *   - dot_add / dot_sub take no carry-in (Alg. 1 starts with c_out = 0);
+ *     the variants take one, and any nonzero carry-in word counts as 1.
  *
  * All functions return 0 on success, -1 on a bad argument.
  */
@@ -251,4 +257,62 @@ int oracle_vnc_pairs(size_t m, int32_t *ia, int32_t *jb, int32_t *ncol)
         ncol[c] = n;
     }
     return t == m * m ? 0 : -3;
+}
+
+/* ---- mpn-style variants: B zero-padded to ma limbs, carry/borrow-in ------ */
+static void add_gen_one(const uint32_t *a, size_t ma, const uint32_t *b, size_t mb,
+                        uint32_t cin, uint32_t *s, uint32_t *carry)
+{
+    uint64_t c = cin ? 1u : 0u;
+    for (size_t i = 0; i < ma; ++i) {
+        const uint64_t bi = i < mb ? (uint64_t)b[i] : 0u;
+        const uint64_t t = (uint64_t)a[i] + bi + c;
+        s[i] = (uint32_t)t;
+        c = t >> 32;
+    }
+    *carry = (uint32_t)c;
+}
+
+static void sub_gen_one(const uint32_t *a, size_t ma, const uint32_t *b, size_t mb,
+                        uint32_t bin, uint32_t *d, uint32_t *borrow)
+{
+    uint64_t br = bin ? 1u : 0u;
+    for (size_t i = 0; i < ma; ++i) {
+        const uint64_t bi = i < mb ? (uint64_t)b[i] : 0u;
+        const uint64_t t = (uint64_t)a[i] - bi - br;   /* bit 63 set iff negative */
+        d[i] = (uint32_t)t;
+        br = t >> 63;
+    }
+    *borrow = (uint32_t)br;
+}
+
+/* a: [batch][ma], b: [batch][mb] (mb <= ma), cin: [batch] or NULL (no
+ * carry-in), s: [batch][ma], carry: [batch] */
+int oracle_add_gen(const uint32_t *a, size_t ma, const uint32_t *b, size_t mb, const uint32_t *cin,
+                   uint32_t *s, uint32_t *carry, size_t batch)
+{
+    if (mb > ma) return -1;
+    if (batch && (!carry || (ma && (!a || !s)) || (mb && !b))) return -1;
+    for (size_t k = 0; k < batch; ++k)
+        add_gen_one(a + k * ma, ma, b + k * mb, mb, cin ? cin[k] : 0u, s + k * ma, carry + k);
+    return 0;
+}
+
+int oracle_sub_gen(const uint32_t *a, size_t ma, const uint32_t *b, size_t mb, const uint32_t *bin,
+                   uint32_t *d, uint32_t *borrow, size_t batch)
+{
+    if (mb > ma) return -1;
+    if (batch && (!borrow || (ma && (!a || !d)) || (mb && !b))) return -1;
+    for (size_t k = 0; k < batch; ++k)
+        sub_gen_one(a + k * ma, ma, b + k * mb, mb, bin ? bin[k] : 0u, d + k * ma, borrow + k);
+    return 0;
+}
+
+/* P = A * A: the definition, through the same row-wise schoolbook */
+int oracle_sqr(const uint32_t *a, uint32_t *p, size_t m, size_t batch)
+{
+    if (batch && m && (!a || !p)) return -1;
+    for (size_t k = 0; k < batch; ++k)
+        mul_one(a + k * m, a + k * m, p + 2 * k * m, m);
+    return 0;
 }

@@ -38,6 +38,13 @@ MUTANTS = [
     ("ragged_carry_slot", "carry + k, (size_t)(off[k + 1] - off[k]));\n    }\n    return 0;\n}\n\nint oracle_sub_ragged",
      "carry + 0, (size_t)(off[k + 1] - off[k]));\n    }\n    return 0;\n}\n\nint oracle_sub_ragged"),
     ("mixed_op_swap", "case 0: add_one", "case 1: add_one"),
+    ("gen_drops_carry_in", "uint64_t c = cin ? 1u : 0u;", "uint64_t c = 0;"),
+    ("gen_pads_with_ones", "const uint64_t bi = i < mb ? (uint64_t)b[i] : 0u;",
+     "const uint64_t bi = i < mb ? (uint64_t)b[i] : 0xFFFFFFFFu;"),
+    ("gen_borrow_in_sign", "const uint64_t t = (uint64_t)a[i] - bi - br;",
+     "const uint64_t t = (uint64_t)a[i] - bi + br;"),
+    ("sqr_first_row_operand", "mul_one(a + k * m, a + k * m, p + 2 * k * m, m);",
+     "mul_one(a + k * m, a, p + 2 * k * m, m);"),
 ]
 
 

@@ -8,6 +8,8 @@
 * invariants: (a + b) - b = a, a - a = 0, a + b = b + a, ab = ba,
   a (b + c) = ab + ac, a * 1 = a, a * 0 = 0, a * X^j = shift;
 * the m = 5 worked example of Alg. 2 (Sec. 3.2), tests/golden;
+* the mpn-style variants (carry-in, zero-padded shorter operand) and the
+  square, against Python's integers and closed forms;
 * the carry-probability lemma of the appendix (Pr[carry] = 1/2 - 2^-(k+1)).
 
 Each pin is a plain function so that tests/test_oracle_mutants.py can rerun it
@@ -233,9 +235,64 @@ def pin_carry_probability():
     assert ((s[:, 0] < x[:, 0]).astype(np.uint32) == c).all()
 
 
+def pin_python_int_variants():
+    """The mpn-style variants (carry-in, one-limb and shorter second
+    operands) and the square, against Python's integers."""
+    g = W.rng(14)
+    for ma, mb in ((1, 0), (1, 1), (2, 1), (3, 1), (7, 3), (32, 32), (33, 1), (129, 64)):
+        for cls in W.CLASSES:
+            x, _ = W.class_operands(g, cls, 6, ma)
+            _, y = W.class_operands(g, cls, 6, max(mb, 1))
+            y = np.ascontiguousarray(y[:, :mb])
+            cin = g.integers(0, 2, 6).astype(np.uint32) * np.uint32(1 + (ma % 3))   # nonzero counts as 1
+            for ci in (None, cin):
+                s, c = oracle.add_gen(x, y, ci)
+                d, br = oracle.sub_gen(x, y, ci)
+                for k in range(6):
+                    A = to_int(x[k])
+                    B = to_int(y[k]) if mb else 0
+                    C = 0 if ci is None else int(ci[k] != 0)
+                    assert to_int(s[k]) + int(c[k]) * X ** ma == A + B + C, (ma, mb, cls, k)
+                    assert to_int(d[k]) - int(br[k]) * X ** ma == A - B - C, (ma, mb, cls, k)
+                    assert int(c[k]) in (0, 1) and int(br[k]) in (0, 1)
+    for m in (1, 2, 3, 5, 8, 31, 64, 129):
+        for cls in W.CLASSES:
+            x, _ = W.class_operands(g, cls, 4, m)
+            p = oracle.sqr(x)
+            for k in range(x.shape[0]):
+                assert to_int(p[k]) == to_int(x[k]) ** 2, (m, cls, k)
+
+
+def pin_closed_forms_variants():
+    for m in (1, 2, 5, 64):
+        ones = np.full((1, m), 0xFFFFFFFF, np.uint32)
+        zeros = np.zeros((1, m), np.uint32)
+        one = np.array([[1]], np.uint32)
+        # (X^m - 1) + 0 + carry-in 1 = X^m
+        s, c = oracle.add_gen(ones, zeros, np.array([1], np.uint32))
+        assert not s.any() and c[0] == 1
+        # 0 - 0 - borrow-in 1 = X^m - 1 with borrow 1
+        d, br = oracle.sub_gen(zeros, zeros, np.array([1], np.uint32))
+        assert (d == 0xFFFFFFFF).all() and br[0] == 1
+        # one-limb operand: (X^m - 1) + 1 = X^m (the carry ripples all m limbs)
+        s, c = oracle.add_gen(ones, one)
+        assert not s.any() and c[0] == 1
+        # X^(m-1) - 1 = (X^(m-1) - 1): the borrow ripples to the top limb
+        top = zeros.copy()
+        top[0, m - 1] = 1
+        d, br = oracle.sub_gen(top, one)
+        want = np.full(m, 0xFFFFFFFF, np.uint32)
+        want[m - 1] = 0
+        assert (d[0] == want).all() and br[0] == 0
+        # (X^m - 1)^2 = X^2m - 2 X^m + 1: limbs 1, 0.., 0xFFFFFFFE, 0xFFFFFFFF..
+        p = oracle.sqr(ones)[0]
+        assert p[0] == 1 and not p[1:m].any() and p[m] == 0xFFFFFFFE and (p[m + 1:] == 0xFFFFFFFF).all()
+
+
 PINS = [pin_python_int_addsub, pin_python_int_mul, pin_python_int_mul_vnc,
         pin_brute_force_small, pin_closed_forms, pin_invariants,
-        pin_vnc_worked_example, pin_ragged_and_mixed, pin_carry_probability]
+        pin_vnc_worked_example, pin_ragged_and_mixed, pin_carry_probability,
+        pin_python_int_variants, pin_closed_forms_variants]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
