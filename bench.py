@@ -549,6 +549,21 @@ def suite(args):
                            "per_sm_clk": IMAD_PER_SM_CLK, "algorithmic_imad_per_product": 2},
               "sizes": rows})
 
+    if want("sqr"):
+        # -- batched square (half the partial products) vs the general product
+        rows = []
+        for m in (32, 128, 256):
+            x, _, _ = W.batched_mul(m)
+            a = dv(x)
+            p = torch.empty((x.shape[0], 2 * m), dtype=torch.int32, device="cuda")
+            t_mul = _event_ms(lambda: dot.mul(a, a, p, ctx=ctx), 20, stream)
+            t_sqr = _event_ms(lambda: dot.sqr(a, p, ctx=ctx), 20, stream)
+            sel = np.random.default_rng(m).integers(0, x.shape[0], 512)
+            ok = np.array_equal(hs(p)[sel], oracle.sqr(x[sel]))
+            rows.append({"m_limbs": m, "ops": x.shape[0], "ms_mul": round(t_mul, 4), "ms_sqr": round(t_sqr, 4),
+                         "speedup_sqr_vs_mul": round(t_mul / t_sqr, 3), "bit_exact_sample": bool(ok)})
+        emit({"workload": "batched square: 2^16 operands at 1024/4096/8192 bits", "sizes": rows})
+
     if want("mixed"):
         # -- mixed ragged batch: one persistent bucketed kernel vs one launch per size
         w = W.ragged_mixed()
@@ -640,7 +655,7 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run only the small ncu case of the dominant kernel")
     ap.add_argument("--launches", type=int, default=3)
-    ap.add_argument("--only", default="", help="--suite rows to run: mix,mul,mixed,shared")
+    ap.add_argument("--only", default="", help="--suite rows to run: mix,mul,sqr,mixed,shared")
     ap.add_argument("--case", choices=["add", "long", "mul", "shared"], default="add",
                     help="which kernel --profile-case runs")
     ap.add_argument("--gpus", type=int, default=1)

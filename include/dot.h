@@ -119,6 +119,44 @@ DOT_API dot_status_t dot_sub_ragged(dot_ctx_t ctx, const uint32_t *a, const uint
                                     uint32_t *d, uint32_t *borrow_out, const uint64_t *off,
                                     size_t batch, dot_stream_t stream);
 
+/* mpn-style variants of the same addition and subtraction -- the library
+ * primitives DoT replaces when integrated into a big-number library (Sec. 3.3,
+ * "Implementation"; the textbook MPN-ADD-M of the appendix takes a carry-in
+ * and operands of different lengths).  All are batched over rows k < batch,
+ * one warp per op; results and carries as dot_add / dot_sub.  s (d) may be a
+ * exactly; other overlaps of outputs with inputs give DOT_EINVAL. */
+
+/* With a carry-in: s[k] + carry_out[k] X^m = a[k] + b[k] + [carry_in[k] != 0].
+ * carry_in: device uint32_t[batch] (required).  m == 0 gives carry_out =
+ * carry_in. */
+DOT_API dot_status_t dot_add_nc(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b,
+                                const uint32_t *carry_in, uint32_t *s, uint32_t *carry_out,
+                                size_t m, size_t batch, dot_stream_t stream);
+/* With a borrow-in: d[k] - borrow_out[k] X^m = a[k] - b[k] - [borrow_in[k] != 0]. */
+DOT_API dot_status_t dot_sub_nc(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b,
+                                const uint32_t *borrow_in, uint32_t *d, uint32_t *borrow_out,
+                                size_t m, size_t batch, dot_stream_t stream);
+
+/* One-limb operand: s[k] + carry_out[k] X^m = a[k] + b[k], where b is
+ * uint32_t[batch] (one limb per op) and a, s are uint32_t[batch][m], m >= 1
+ * (m == 0 with batch > 0: DOT_EINVAL). */
+DOT_API dot_status_t dot_add_1(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b, uint32_t *s,
+                               uint32_t *carry_out, size_t m, size_t batch, dot_stream_t stream);
+DOT_API dot_status_t dot_sub_1(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b, uint32_t *d,
+                               uint32_t *borrow_out, size_t m, size_t batch, dot_stream_t stream);
+
+/* Unequal lengths: a is uint32_t[batch][ma], b is uint32_t[batch][mb] with
+ * mb <= ma (else DOT_EINVAL), taken as zero-padded to ma limbs (the padding
+ * of Theorem 2's proof); s: uint32_t[batch][ma] with
+ * s[k] + carry_out[k] X^ma = a[k] + b[k] (d[k] - borrow_out[k] X^ma =
+ * a[k] - b[k]).  ma == 0 gives carry 0. */
+DOT_API dot_status_t dot_add_unequal(dot_ctx_t ctx, const uint32_t *a, size_t ma, const uint32_t *b,
+                                     size_t mb, uint32_t *s, uint32_t *carry_out, size_t batch,
+                                     dot_stream_t stream);
+DOT_API dot_status_t dot_sub_unequal(dot_ctx_t ctx, const uint32_t *a, size_t ma, const uint32_t *b,
+                                     size_t mb, uint32_t *d, uint32_t *borrow_out, size_t batch,
+                                     dot_stream_t stream);
+
 /* --------------------------------------------------------------- multiply --- */
 
 /* Batched product, Alg. 2 (DoT-Mul-Words) and Theorem 2 (Sec. 3.2):
@@ -128,6 +166,14 @@ DOT_API dot_status_t dot_sub_ragged(dot_ctx_t ctx, const uint32_t *a, const uint
  * pass.  1 <= m <= DOT_MUL_MAX_LIMBS, else DOT_EUNSUPPORTED (m == 0: no-op). */
 DOT_API dot_status_t dot_mul(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b,
                              uint32_t *p, size_t m, size_t batch, dot_stream_t stream);
+
+/* Batched square, p[k] = a[k]^2 as 2m limbs: Theorem 2 (Sec. 3.2) with
+ * A = B, where each column sum is twice the sum over the pairs i < j plus
+ * the diagonal square A_{c/2}^2 -- half the partial products of dot_mul.
+ * a: uint32_t[batch][m]; p: uint32_t[batch][2m], no overlap with a.
+ * 1 <= m <= DOT_MUL_MAX_LIMBS, else DOT_EUNSUPPORTED (m == 0: no-op). */
+DOT_API dot_status_t dot_sqr(dot_ctx_t ctx, const uint32_t *a, uint32_t *p, size_t m, size_t batch,
+                             dot_stream_t stream);
 
 /* Ragged product: op k has m_k = off[k+1] - off[k] limbs (<= DOT_MUL_MAX_LIMBS,
  * larger ops record DOT_EUNSUPPORTED in the ctx and are skipped); its 2 m_k
@@ -141,9 +187,11 @@ DOT_API dot_status_t dot_mul_ragged(dot_ctx_t ctx, const uint32_t *a, const uint
  * overlap with the inputs).  The column sums of Theorem 2 (Sec. 3.2) over
  * 8-bit digits of a fixed operand form one matrix product with a Toeplitz
  * matrix; use_tensor_cores != 0 runs it on the tensor cores (tcgen05.mma,
- * fp16 digits, fp32 accumulation -- exact because every column sum is at
- * most 256 * 255^2 < 2^24) and normalises the carries in the epilogue; it
- * needs 1 <= m <= 64 (2048 bits), else DOT_EUNSUPPORTED.  use_tensor_cores
+ * fp16 digits -- the batch's shifted by -128, the fixed operand's balanced
+ * to [-128, 128] -- with fp32 accumulation, exact because every partial sum
+ * stays an integer within 2^22 of the accumulator's start 1.5 * 2^23) and
+ * normalises the carries in the epilogue; it needs 1 <= m <= 64 (2048
+ * bits), else DOT_EUNSUPPORTED.  use_tensor_cores
  * == 0 runs the INT32 column-sum path of dot_mul (m <= DOT_MUL_MAX_LIMBS). */
 DOT_API dot_status_t dot_mul_shared(dot_ctx_t ctx, const uint32_t *fixed, const uint32_t *b,
                                     uint32_t *p, size_t m, size_t batch, int use_tensor_cores,

@@ -16,6 +16,7 @@
 #include "dot_internal.cuh"
 #include "dot_plan.h"
 #include "dot_addsub.cuh"
+#include "dot_warp_op.cuh"
 
 #define WARP_KERNEL_THREADS 256
 
@@ -406,7 +407,24 @@ addsub_ragged_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint32_t
             }
             continue;
         }
-        addsub_warp_op<SUB>(a + lo, b + lo, s + lo, (size_t)(hi - lo), cout + op);
+        addsub_warp_op<SUB>(a + lo, b + lo, s + lo, (size_t)(hi - lo), cout + op, (size_t)(hi - lo), 0u);
+    }
+}
+
+// ============================ general add/sub: carry-in, unequal lengths
+// Op i: a_i (ma limbs) +/- b_i (mb <= ma limbs, zero-extended) + cin_i, the
+// ma-limb result and its carry/borrow out; cin may be null (no carry-in), a
+// nonzero cin_i counts as 1.  One warp per op (the mpn-style variants).
+template <bool SUB>
+__global__ void __launch_bounds__(WARP_KERNEL_THREADS)
+addsub_general_kernel(const uint32_t *a, const uint32_t *b, const uint32_t *cin, uint32_t *s, uint32_t *cout,
+                      size_t ma, size_t mb, size_t batch)
+{
+    const size_t warp_global = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const size_t nwarps = ((size_t)gridDim.x * blockDim.x) >> 5;
+    for (size_t op = warp_global; op < batch; op += nwarps) {
+        const uint32_t c = cin ? (uint32_t)(cin[op] != 0u) : 0u;
+        addsub_warp_op<SUB>(a + op * ma, b + op * mb, s + op * ma, ma, cout + op, mb, c);
     }
 }
 
@@ -526,6 +544,32 @@ static dot_status_t addsub_ragged(dot_ctx_t ctx, const uint32_t *a, const uint32
     return cudaGetLastError() == cudaSuccess ? DOT_OK : DOT_ECUDA;
 }
 
+template <bool SUB>
+static dot_status_t addsub_general(dot_ctx_t ctx, const uint32_t *a, size_t ma, const uint32_t *b, size_t mb,
+                                   const uint32_t *cin, uint32_t *s, uint32_t *cout, size_t batch, cudaStream_t st)
+{
+    dot_status_t rc = dot_check_ctx(ctx);
+    if (rc != DOT_OK) return rc;
+    if (batch == 0) return DOT_OK;
+    if (mb > ma || !cout) return DOT_EINVAL;
+    if ((ma && (!a || !s)) || (mb && !b)) return DOT_EINVAL;
+    if (ma > SIZE_MAX / 4 / batch) return DOT_EINVAL;
+    const size_t abytes = ma * batch * 4, bbytes = mb * batch * 4, cbytes = batch * 4;
+    // s may be a exactly; s may be b exactly only when the rows have the same stride
+    if (partial_overlap(s, abytes, a, abytes) || (mb != ma ? any_overlap(s, abytes, b, bbytes)
+                                                           : partial_overlap(s, abytes, b, bbytes)))
+        return DOT_EINVAL;
+    if (any_overlap(cout, cbytes, s, abytes) || any_overlap(cout, cbytes, a, abytes) ||
+        any_overlap(cout, cbytes, b, bbytes))
+        return DOT_EINVAL;
+    const void *fn = (const void *)addsub_general_kernel<SUB>;
+    const size_t cap = (size_t)ctx->num_sms * dot_blocks_per_sm(fn, WARP_KERNEL_THREADS, 0);
+    const size_t need = dot_ceil_div(batch, WARP_KERNEL_THREADS / 32);
+    const unsigned grid = (unsigned)(need < cap ? need : cap);
+    addsub_general_kernel<SUB><<<grid, WARP_KERNEL_THREADS, 0, st>>>(a, b, cin, s, cout, ma, mb, batch);
+    return cudaGetLastError() == cudaSuccess ? DOT_OK : DOT_ECUDA;
+}
+
 extern "C" {
 
 DOT_API dot_status_t dot_add(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b, uint32_t *s,
@@ -552,6 +596,46 @@ DOT_API dot_status_t dot_sub_ragged(dot_ctx_t ctx, const uint32_t *a, const uint
                                     dot_stream_t stream)
 {
     return addsub_ragged<true>(ctx, a, b, d, borrow_out, off, batch, (cudaStream_t)stream);
+}
+
+DOT_API dot_status_t dot_add_nc(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b, const uint32_t *carry_in,
+                                uint32_t *s, uint32_t *carry_out, size_t m, size_t batch, dot_stream_t stream)
+{
+    if (!carry_in && batch) return DOT_EINVAL;
+    return addsub_general<false>(ctx, a, m, b, m, carry_in, s, carry_out, batch, (cudaStream_t)stream);
+}
+
+DOT_API dot_status_t dot_sub_nc(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b, const uint32_t *borrow_in,
+                                uint32_t *d, uint32_t *borrow_out, size_t m, size_t batch, dot_stream_t stream)
+{
+    if (!borrow_in && batch) return DOT_EINVAL;
+    return addsub_general<true>(ctx, a, m, b, m, borrow_in, d, borrow_out, batch, (cudaStream_t)stream);
+}
+
+DOT_API dot_status_t dot_add_1(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b, uint32_t *s,
+                               uint32_t *carry_out, size_t m, size_t batch, dot_stream_t stream)
+{
+    if (m == 0 && batch) return DOT_EINVAL;
+    return addsub_general<false>(ctx, a, m, b, 1, nullptr, s, carry_out, batch, (cudaStream_t)stream);
+}
+
+DOT_API dot_status_t dot_sub_1(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b, uint32_t *d,
+                               uint32_t *borrow_out, size_t m, size_t batch, dot_stream_t stream)
+{
+    if (m == 0 && batch) return DOT_EINVAL;
+    return addsub_general<true>(ctx, a, m, b, 1, nullptr, d, borrow_out, batch, (cudaStream_t)stream);
+}
+
+DOT_API dot_status_t dot_add_unequal(dot_ctx_t ctx, const uint32_t *a, size_t ma, const uint32_t *b, size_t mb,
+                                     uint32_t *s, uint32_t *carry_out, size_t batch, dot_stream_t stream)
+{
+    return addsub_general<false>(ctx, a, ma, b, mb, nullptr, s, carry_out, batch, (cudaStream_t)stream);
+}
+
+DOT_API dot_status_t dot_sub_unequal(dot_ctx_t ctx, const uint32_t *a, size_t ma, const uint32_t *b, size_t mb,
+                                     uint32_t *d, uint32_t *borrow_out, size_t batch, dot_stream_t stream)
+{
+    return addsub_general<true>(ctx, a, ma, b, mb, nullptr, d, borrow_out, batch, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -20,6 +20,7 @@
 #include "dot_internal.cuh"
 #include "dot_plan.h"
 #include "dot_addsub.cuh"
+#include "dot_warp_op.cuh"
 #include "dot_mul.cuh"
 
 // bucket ids, in processing order
@@ -204,9 +205,9 @@ mixed_run(const dot_desc_t *desc, const uint32_t *order, MixedMeta *meta, const 
             const uint32_t op = order[base + k0];
             const dot_desc_t d = desc[op];
             if (d.op == DOT_OP_SUB)
-                addsub_warp_op<true>(a + d.a_off, b + d.b_off, r + d.r_off, d.m, carry + op);
+                addsub_warp_op<true>(a + d.a_off, b + d.b_off, r + d.r_off, d.m, carry + op, d.m, 0u);
             else
-                addsub_warp_op<false>(a + d.a_off, b + d.b_off, r + d.r_off, d.m, carry + op);
+                addsub_warp_op<false>(a + d.a_off, b + d.b_off, r + d.r_off, d.m, carry + op, d.m, 0u);
         }
         }
     }

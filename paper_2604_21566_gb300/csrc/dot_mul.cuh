@@ -92,6 +92,70 @@ __device__ __forceinline__ void colsum_block(const uint32_t *As, const uint32_t 
     cols_to_positional<R>(s0, s1, s2, W);
 }
 
+// One column: (s2:s1:s0) += a * w
+__device__ __forceinline__ void mac1(uint32_t &s0, uint32_t &s1, uint32_t &s2, uint32_t a, uint32_t w)
+{
+    asm("{\n\t.reg .u32 lo, hi;\n\t"
+        "mul.lo.u32 lo, %3, %4;\n\t"
+        "mul.hi.u32 hi, %3, %4;\n\t"
+        "add.cc.u32 %0, %0, lo;\n\t"
+        "addc.cc.u32 %1, %1, hi;\n\t"
+        "addc.u32 %2, %2, 0;\n\t}"
+        : "+r"(s0), "+r"(s1), "+r"(s2)
+        : "r"(a), "r"(w));
+}
+
+// The same block for a square, A = B (As and Bs hold the same operand):
+// S_c = 2 sum_{i<j, i+j=c} A_i A_j + [c even] A_{c/2}^2, so only rows with
+// 2i < c are summed (about half of them), doubled, and the diagonal square
+// added.  Rows with 2i < c0 feed every column of the block and use the
+// sliding window; the few rows with c0 <= 2i < c0 + R feed only the columns
+// c > 2i and are summed one column at a time.
+template <int R>
+__device__ __forceinline__ void sqr_colsum_block(const uint32_t *As, const uint32_t *Bs, int c0, int mp,
+                                                 uint32_t (&W)[R + 2])
+{
+    uint32_t s0[R], s1[R], s2[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) s0[k] = s1[k] = s2[k] = 0;
+    const int i_lo = max(0, c0 - mp + 1);
+    const int i_full = min((c0 - 1) >> 1, mp - 1);   // last row with 2i < c0 (-1: none)
+    int i0 = (i_lo / R) * R;
+    if (i0 + R - 1 <= i_full) {
+        uint32_t w[R];
+        lds_vec<R>(Bs + R + (c0 - i0), w);   // w[k] = A[c0 + k - i0]
+        for (; i0 + R - 1 <= i_full; i0 += R) {
+#pragma unroll
+            for (int ii = 0; ii < R; ++ii) {
+                mac_cols<R>(s0, s1, s2, As[i0 + ii], w);
+#pragma unroll
+                for (int k = R - 1; k > 0; --k) w[k] = w[k - 1];
+                w[0] = Bs[R + c0 - (i0 + ii) - 1];
+            }
+        }
+    }
+    const int i_top = min((c0 + R - 1) >> 1, mp - 1);   // last row with 2i < c0 + R
+    for (int i = i0; i <= i_top; ++i) {
+        const uint32_t ai = As[i];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int j = c0 + k - i;   // j > i >= 0; A is zero past m
+            mac1(s0[k], s1[k], s2[k], ai, j > i ? Bs[R + j] : 0u);
+        }
+    }
+    // double the off-diagonal sums, add the squares A_{c/2}^2 of even columns
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        s2[k] = (s2[k] << 1) | (s1[k] >> 31);
+        s1[k] = (s1[k] << 1) | (s0[k] >> 31);
+        s0[k] <<= 1;
+        const int c = c0 + k;
+        const uint32_t d = (c & 1) ? 0u : As[c >> 1];
+        mac1(s0[k], s1[k], s2[k], d, d);
+    }
+    cols_to_positional<R>(s0, s1, s2, W);
+}
+
 // Copy limbs [t R, t R + R) of an m-limb row into shared memory (zeros past m).
 template <int R>
 __device__ __forceinline__ void stage_row(const uint32_t *row, uint32_t *dst, int t, int m, bool vec)
@@ -127,7 +191,7 @@ __device__ __forceinline__ void store_block(uint32_t *row, int pos, int len, con
 // part without touching memory.  The low half of the product is resolved and
 // stored before the high blocks are summed, so only its carry-out and the two
 // overflow words of the top low block are kept across.
-template <int R>
+template <int R, bool SQR = false>
 __device__ __forceinline__ void mul_group(const uint32_t *As, const uint32_t *Bs, int t, int T,
                                           int tn, int grp, bool on, int m, int mp, uint32_t *prow,
                                           bool vec_out, uint32_t smask, uint32_t tmask)
@@ -139,7 +203,8 @@ __device__ __forceinline__ void mul_group(const uint32_t *As, const uint32_t *Bs
     uint32_t wl, wh, mid;
     {   // low blocks [tR, tR + R): positions 0 .. m' - 1
         if (on) {
-            colsum_block<R>(As, Bs, t * R, mp, W);
+            if (SQR) sqr_colsum_block<R>(As, Bs, t * R, mp, W);
+            else colsum_block<R>(As, Bs, t * R, mp, W);
         } else {
 #pragma unroll
             for (int k = 0; k < R + 2; ++k) W[k] = 0;
@@ -166,7 +231,8 @@ __device__ __forceinline__ void mul_group(const uint32_t *As, const uint32_t *Bs
     }
     {   // high blocks [m' + tR, m' + tR + R)
         if (on) {
-            colsum_block<R>(As, Bs, mp + t * R, mp, W);
+            if (SQR) sqr_colsum_block<R>(As, Bs, mp + t * R, mp, W);
+            else colsum_block<R>(As, Bs, mp + t * R, mp, W);
         } else {
 #pragma unroll
             for (int k = 0; k < R + 2; ++k) W[k] = 0;

@@ -73,6 +73,13 @@ _SIGS = {
     "dot_mul_host": (_st, [_vp, _vp, _vp, _vp, _sz, _sz, _vp]),
     "dot_add_noalloc": (_st, [ctypes.c_int, _vp, _vp, _vp, _vp, _sz, _sz, _vp]),
     "dot_mul_shared": (_st, [_vp, _vp, _vp, _vp, _sz, _sz, ctypes.c_int, _vp]),
+    "dot_add_nc": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _sz, _vp]),
+    "dot_sub_nc": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _sz, _vp]),
+    "dot_add_1": (_st, [_vp, _vp, _vp, _vp, _vp, _sz, _sz, _vp]),
+    "dot_sub_1": (_st, [_vp, _vp, _vp, _vp, _vp, _sz, _sz, _vp]),
+    "dot_add_unequal": (_st, [_vp, _vp, _sz, _vp, _sz, _vp, _vp, _sz, _vp]),
+    "dot_sub_unequal": (_st, [_vp, _vp, _sz, _vp, _sz, _vp, _vp, _sz, _vp]),
+    "dot_sqr": (_st, [_vp, _vp, _vp, _sz, _sz, _vp]),
     "dot_tune_set": (_st, [_vp, ctypes.c_int, _sz, ctypes.c_int]),
     "dot_tune_get": (_st, [_vp, ctypes.c_int, _sz, ctypes.POINTER(ctypes.c_int)]),
     "dot_autotune": (_st, [_vp, ctypes.c_int, _sz, _sz, ctypes.POINTER(ctypes.c_int),
@@ -258,6 +265,96 @@ def mul(a, b, out=None, ctx=None, stream=None):
         raise ValueError("dot_mul: out must be [batch, 2m]")
     ctx = ctx or default_context(a.device.index)
     _chk(lib().dot_mul(ctx.handle, _ptr(a), _ptr(b), _ptr(out), m, batch, _stream(stream)), "dot_mul")
+    return out
+
+
+def _carry_like(a, carry):
+    import torch
+    return torch.empty(a.shape[0], dtype=a.dtype, device=a.device) if carry is None else carry
+
+
+def add_nc(a, b, carry_in, out=None, carry=None, ctx=None, stream=None, sub=False):
+    """(s, carry) with s + carry X^m = a + b + [carry_in != 0], row by row
+    (with sub=True: d - borrow X^m = a - b - [borrow_in != 0])."""
+    import torch
+    out = torch.empty_like(a) if out is None else out
+    carry = _carry_like(a, carry)
+    for t, n in ((a, "a"), (b, "b"), (carry_in, "carry_in"), (out, "out"), (carry, "carry")):
+        _limb_tensor(t, n)
+    what = "dot_sub_nc" if sub else "dot_add_nc"
+    if a.dim() != 2 or a.shape != b.shape or out.shape != a.shape or carry_in.numel() != a.shape[0] \
+            or carry.numel() != a.shape[0]:
+        raise ValueError(f"{what}: a, b, out [batch, m]; carry_in, carry [batch]")
+    batch, m = a.shape
+    ctx = ctx or default_context(a.device.index)
+    fn = lib().dot_sub_nc if sub else lib().dot_add_nc
+    _chk(fn(ctx.handle, _ptr(a), _ptr(b), _ptr(carry_in), _ptr(out), _ptr(carry), m, batch, _stream(stream)),
+         what)
+    return out, carry
+
+
+def sub_nc(a, b, borrow_in, out=None, borrow=None, ctx=None, stream=None):
+    return add_nc(a, b, borrow_in, out, borrow, ctx, stream, sub=True)
+
+
+def add_1(a, b, out=None, carry=None, ctx=None, stream=None, sub=False):
+    """(s, carry) with s + carry X^m = a + b for a one-limb b[k] per row."""
+    import torch
+    out = torch.empty_like(a) if out is None else out
+    carry = _carry_like(a, carry)
+    for t, n in ((a, "a"), (b, "b"), (out, "out"), (carry, "carry")):
+        _limb_tensor(t, n)
+    what = "dot_sub_1" if sub else "dot_add_1"
+    if a.dim() != 2 or out.shape != a.shape or b.numel() != a.shape[0] or carry.numel() != a.shape[0]:
+        raise ValueError(f"{what}: a, out [batch, m]; b, carry [batch]")
+    batch, m = a.shape
+    ctx = ctx or default_context(a.device.index)
+    fn = lib().dot_sub_1 if sub else lib().dot_add_1
+    _chk(fn(ctx.handle, _ptr(a), _ptr(b), _ptr(out), _ptr(carry), m, batch, _stream(stream)), what)
+    return out, carry
+
+
+def sub_1(a, b, out=None, borrow=None, ctx=None, stream=None):
+    return add_1(a, b, out, borrow, ctx, stream, sub=True)
+
+
+def add_unequal(a, b, out=None, carry=None, ctx=None, stream=None, sub=False):
+    """(s, carry) with s + carry X^ma = a + b for a: [batch, ma], b: [batch, mb], mb <= ma."""
+    import torch
+    out = torch.empty_like(a) if out is None else out
+    carry = _carry_like(a, carry)
+    for t, n in ((a, "a"), (b, "b"), (out, "out"), (carry, "carry")):
+        _limb_tensor(t, n)
+    what = "dot_sub_unequal" if sub else "dot_add_unequal"
+    if a.dim() != 2 or b.dim() != 2 or b.shape[0] != a.shape[0] or out.shape != a.shape \
+            or carry.numel() != a.shape[0]:
+        raise ValueError(f"{what}: a, out [batch, ma]; b [batch, mb]; carry [batch]")
+    batch, ma = a.shape
+    mb = b.shape[1]
+    ctx = ctx or default_context(a.device.index)
+    fn = lib().dot_sub_unequal if sub else lib().dot_add_unequal
+    _chk(fn(ctx.handle, _ptr(a), ma, _ptr(b), mb, _ptr(out), _ptr(carry), batch, _stream(stream)), what)
+    return out, carry
+
+
+def sub_unequal(a, b, out=None, borrow=None, ctx=None, stream=None):
+    return add_unequal(a, b, out, borrow, ctx, stream, sub=True)
+
+
+def sqr(a, out=None, ctx=None, stream=None):
+    """p = a^2 as 2m limbs, row by row (half the partial products of mul)."""
+    import torch
+    _limb_tensor(a, "a")
+    if a.dim() != 2:
+        raise ValueError("dot_sqr: a must be [batch, m]")
+    batch, m = a.shape
+    if out is None:
+        out = torch.empty((batch, 2 * m), dtype=a.dtype, device=a.device)
+    _limb_tensor(out, "out")
+    if tuple(out.shape) != (batch, 2 * m):
+        raise ValueError("dot_sqr: out must be [batch, 2m]")
+    ctx = ctx or default_context(a.device.index)
+    _chk(lib().dot_sqr(ctx.handle, _ptr(a), _ptr(out), m, batch, _stream(stream)), "dot_sqr")
     return out
 
 
