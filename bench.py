@@ -564,6 +564,27 @@ def suite(args):
                          "speedup_sqr_vs_mul": round(t_mul / t_sqr, 3), "bit_exact_sample": bool(ok)})
         emit({"workload": "batched square: 2^16 operands at 1024/4096/8192 bits", "sizes": rows})
 
+    if want("kara"):
+        # -- Karatsuba above the base case: effective schoolbook limb products per second
+        rows = []
+        for m, batch in ((1024, 4096), (2048, 2048), (4096, 1024), (8192, 256)):
+            g = np.random.default_rng(5000 + m)
+            x = g.integers(0, 2 ** 32, (batch, m), dtype=np.uint64).astype(np.uint32)
+            y = g.integers(0, 2 ** 32, (batch, m), dtype=np.uint64).astype(np.uint32)
+            a, b = dv(x), dv(y)
+            p = torch.empty((batch, 2 * m), dtype=torch.int32, device="cuda")
+            ms = _event_ms(lambda: dot.mul_karatsuba(a, b, p, ctx=ctx), 5, stream)
+            sel = np.arange(0, batch, max(1, batch // 4))
+            ok = np.array_equal(hs(p)[sel], oracle.mul(x[sel], y[sel], threads=8))
+            prods = batch * m * m
+            rows.append({"m_limbs": m, "bits": 32 * m, "ops": batch, "ms": round(ms, 4),
+                         "gop_s": round(batch / (ms * 1e-3) / 1e9, 6),
+                         "schoolbook_equiv_tera_products_s": round(prods / (ms * 1e-3) / 1e12, 3),
+                         "bit_exact_sample": bool(ok)})
+        emit({"workload": "Karatsuba above 512 limbs: 32k..262k-bit products",
+              "note": "schoolbook-equivalent rate = batch m^2 / time (m^2 products a schoolbook would do)",
+              "sizes": rows})
+
     if want("mixed"):
         # -- mixed ragged batch: one persistent bucketed kernel vs one launch per size
         w = W.ragged_mixed()
@@ -655,7 +676,7 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run only the small ncu case of the dominant kernel")
     ap.add_argument("--launches", type=int, default=3)
-    ap.add_argument("--only", default="", help="--suite rows to run: mix,mul,sqr,mixed,shared")
+    ap.add_argument("--only", default="", help="--suite rows to run: mix,mul,sqr,kara,mixed,shared")
     ap.add_argument("--case", choices=["add", "long", "mul", "shared"], default="add",
                     help="which kernel --profile-case runs")
     ap.add_argument("--gpus", type=int, default=1)

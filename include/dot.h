@@ -60,6 +60,8 @@ enum { DOT_OP_ADD = 0, DOT_OP_SUB = 1, DOT_OP_MUL = 2 };
 
 /* Largest operand (limbs) of the column-sum multiply kernels. */
 #define DOT_MUL_MAX_LIMBS 512
+/* Largest operand (limbs) of dot_mul_karatsuba (2^25 bits). */
+#define DOT_KARA_MAX_LIMBS (1u << 20)
 
 typedef struct dot_ctx *dot_ctx_t;
 typedef void *dot_stream_t;   /* cudaStream_t */
@@ -174,6 +176,20 @@ DOT_API dot_status_t dot_mul(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b
  * 1 <= m <= DOT_MUL_MAX_LIMBS, else DOT_EUNSUPPORTED (m == 0: no-op). */
 DOT_API dot_status_t dot_sqr(dot_ctx_t ctx, const uint32_t *a, uint32_t *p, size_t m, size_t batch,
                              dot_stream_t stream);
+
+/* Batched product of any size, p[k] = a[k] * b[k] as 2m limbs: the
+ * appendix's MPN-KARATSUBA (Karatsuba, or Toom-Cook 2-way), whose recursion
+ * bottoms out at the base case (Sec. 2): above DOT_MUL_MAX_LIMBS limbs each
+ * level splits at h = ceil(m / 2), forms |A_H - A_L| and |B_H - B_L| with
+ * their signs, runs the three half-size products as one batched product
+ * over 3 x batch operations, and combines P1 b^2 + (P1 + P0 - P2) b + P0 on
+ * the add path; at or below DOT_MUL_MAX_LIMBS it is dot_mul.  Layout as
+ * dot_mul; 1 <= m <= DOT_KARA_MAX_LIMBS (else DOT_EINVAL), m == 0 no-op.
+ * Uses a workspace owned by ctx (about 14 m batch bytes per level, grown on
+ * demand with a device synchronisation; DOT_ENOMEM if it cannot grow):
+ * calls on one ctx must not overlap on the GPU. */
+DOT_API dot_status_t dot_mul_karatsuba(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b,
+                                       uint32_t *p, size_t m, size_t batch, dot_stream_t stream);
 
 /* Ragged product: op k has m_k = off[k+1] - off[k] limbs (<= DOT_MUL_MAX_LIMBS,
  * larger ops record DOT_EUNSUPPORTED in the ctx and are skipped); its 2 m_k

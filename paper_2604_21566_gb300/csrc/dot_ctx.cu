@@ -100,6 +100,7 @@ DOT_API void dot_ctx_destroy(dot_ctx_t c)
     for (int i = 0; i < 2; ++i)
         if (c->side[i]) cudaStreamDestroy(c->side[i]);
     if (c->d_stage) cudaFree(c->d_stage);
+    if (c->d_work) cudaFree(c->d_work);
     if (c->d_tile_state) cudaFree(c->d_tile_state);
     if (c->d_counters) cudaFree(c->d_counters);
     if (c->d_status) cudaFree(c->d_status);
@@ -163,5 +164,19 @@ dot_status_t dot_lookback_prepare(dot_ctx_t c, size_t tiles, LookbackArgs *out)
     out->status = c->d_status;
     out->wait_limit_ns = c->wait_limit_ns;
     out->skip_tile = c->debug_skip_tile;
+    return DOT_OK;
+}
+
+dot_status_t dot_work(dot_ctx_t c, size_t bytes, void **out)
+{
+    if (bytes > c->work_bytes) {
+        void *p = nullptr;
+        if (cudaDeviceSynchronize() != cudaSuccess) return DOT_ECUDA;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) return DOT_ENOMEM;
+        if (c->d_work) cudaFree(c->d_work);
+        c->d_work = p;
+        c->work_bytes = bytes;
+    }
+    *out = c->d_work;
     return DOT_OK;
 }

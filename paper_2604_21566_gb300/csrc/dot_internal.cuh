@@ -41,7 +41,15 @@ struct dot_ctx {
     void *mixed;
     // tuned shape per (op, bit length of m); 0 = built-in choice (dot_tune.cu)
     unsigned char tune[3][65];
+    // general workspace (Karatsuba levels), grown on demand by dot_work
+    void *d_work;
+    size_t work_bytes;
 };
+
+// A device workspace of at least `bytes` (256-byte aligned) owned by the ctx;
+// growing it synchronises the device.  Calls that use it on one ctx must not
+// overlap on the GPU.
+dot_status_t dot_work(dot_ctx_t ctx, size_t bytes, void **out);
 
 void dot_mixed_release(dot_ctx_t ctx);
 

@@ -80,6 +80,7 @@ _SIGS = {
     "dot_add_unequal": (_st, [_vp, _vp, _sz, _vp, _sz, _vp, _vp, _sz, _vp]),
     "dot_sub_unequal": (_st, [_vp, _vp, _sz, _vp, _sz, _vp, _vp, _sz, _vp]),
     "dot_sqr": (_st, [_vp, _vp, _vp, _sz, _sz, _vp]),
+    "dot_mul_karatsuba": (_st, [_vp, _vp, _vp, _vp, _sz, _sz, _vp]),
     "dot_tune_set": (_st, [_vp, ctypes.c_int, _sz, ctypes.c_int]),
     "dot_tune_get": (_st, [_vp, ctypes.c_int, _sz, ctypes.POINTER(ctypes.c_int)]),
     "dot_autotune": (_st, [_vp, ctypes.c_int, _sz, _sz, ctypes.POINTER(ctypes.c_int),
@@ -339,6 +340,24 @@ def add_unequal(a, b, out=None, carry=None, ctx=None, stream=None, sub=False):
 
 def sub_unequal(a, b, out=None, borrow=None, ctx=None, stream=None):
     return add_unequal(a, b, out, borrow, ctx, stream, sub=True)
+
+
+def mul_karatsuba(a, b, out=None, ctx=None, stream=None):
+    """p = a * b as 2m limbs for any m: Karatsuba levels above the base case."""
+    import torch
+    _limb_tensor(a, "a"), _limb_tensor(b, "b")
+    if a.dim() != 2 or a.shape != b.shape:
+        raise ValueError("dot_mul_karatsuba: a, b must be [batch, m] of one shape")
+    batch, m = a.shape
+    if out is None:
+        out = torch.empty((batch, 2 * m), dtype=a.dtype, device=a.device)
+    _limb_tensor(out, "out")
+    if tuple(out.shape) != (batch, 2 * m):
+        raise ValueError("dot_mul_karatsuba: out must be [batch, 2m]")
+    ctx = ctx or default_context(a.device.index)
+    _chk(lib().dot_mul_karatsuba(ctx.handle, _ptr(a), _ptr(b), _ptr(out), m, batch, _stream(stream)),
+         "dot_mul_karatsuba")
+    return out
 
 
 def sqr(a, out=None, ctx=None, stream=None):
