@@ -92,6 +92,7 @@
 // fp32 bits of the accumulator start value M = 1.5 * 2^23 = 3072 * 4096
 #define TZ_MAGIC_BITS 0x4B400000u
 #define TZ_TROWS 384             // stacked Toeplitz rows (3 blocks)
+static_assert(TZ_DIGITS <= TZ_THREADS, "one balanced digit per thread");
 // Toeplitz chunk (d, n, k chunk) holds digits a[s0], a[s0-1], .., a[s0-7],
 // s0 = 128 d + n - 8 kc in [-120, 383]; with r[i] = a[383 - i] that run is
 // r[383 - s0 .. + 7], which the shifted copy (383 - s0) % 8 holds 16-byte aligned
@@ -368,17 +369,21 @@ __device__ __forceinline__ int tz_epilogue(Mid mid, uint32_t tmem, int h, int qu
             tz_fence_before();
             tz_warp_arrive(bar_free);
         }
+        // the limb values first (independent of each other), then the carry
+        // chain, which costs two dependent adds per limb
+        uint64_t L[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int l = 8 * pass + j;
             const uint4 k4 = kq[l >> 2];
             const uint32_t k = (l & 3) == 0 ? k4.x : (l & 3) == 1 ? k4.y : (l & 3) == 2 ? k4.z : k4.w;
-            uint64_t acc = (uint64_t)k + hi;
-            acc += v[4 * j];
-            acc += (uint64_t)v[4 * j + 1] * 256u;
-            acc += (uint64_t)v[4 * j + 2] * 65536u;
-            acc += (uint64_t)v[4 * j + 3] * 16777216u;
-            o[l] = (uint32_t)acc;
+            L[j] = (uint64_t)k + v[4 * j] + (uint64_t)v[4 * j + 1] * 256u + (uint64_t)v[4 * j + 2] * 65536u +
+                   (uint64_t)v[4 * j + 3] * 16777216u;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint64_t acc = L[j] + hi;
+            o[8 * pass + j] = (uint32_t)acc;
             hi = (uint32_t)(acc >> 32);
         }
     }
@@ -606,7 +611,14 @@ toeplitz_mma_kernel(const uint32_t *fixed, const uint32_t *b, uint32_t *p, int m
     const CUtensorMap *pmap = use_map ? &pmap_param : nullptr;
     const int nd = 4 * m;   // digits of each operand
 
-    // the first tile's limbs are in flight during the set-up
+    // the fixed operand's digits first (their latency gates the set-up), then
+    // the first tile's limbs, in flight during the set-up
+    uint32_t dk_word = 0, dp_word = 0;
+    const int kdig = tid;   // TZ_DIGITS <= TZ_THREADS: one digit per thread
+    if (kdig < TZ_DIGITS) {
+        if (kdig < nd) dk_word = fixed[kdig >> 2];
+        if (kdig >= 1 && kdig - 1 < nd) dp_word = fixed[(kdig - 1) >> 2];
+    }
     uint32_t x[16];
     if (tid < TZ_WORKERS && blockIdx.x < ntiles) tz_load(x, b, m, batch, blockIdx.x, tid);
     if (issuer) {
@@ -637,10 +649,10 @@ toeplitz_mma_kernel(const uint32_t *fixed, const uint32_t *b, uint32_t *p, int m
         *reinterpret_cast<uint4 *>(sBias + 16 * i) = make_uint4(first, 0u, 0u, 0u);
     }
     // balanced digits a_k = d_k + [d_{k-1} >= 128] - 256 [d_k >= 128], k <= 4m
-    for (int k = tid; k < TZ_DIGITS; k += TZ_THREADS) {
-        const uint32_t dk = k < nd ? (fixed[k >> 2] >> (8 * (k & 3))) & 0xFFu : 0u;
-        const uint32_t dp = (k >= 1 && k - 1 < nd) ? (fixed[(k - 1) >> 2] >> (8 * ((k - 1) & 3))) & 0xFFu : 0u;
-        dig[k] = (int32_t)dk + (int32_t)(dp >= 128u) - 256 * (int32_t)(dk >= 128u);
+    if (kdig < TZ_DIGITS) {
+        const uint32_t dk = (dk_word >> (8 * (kdig & 3))) & 0xFFu;
+        const uint32_t dp = kdig >= 1 ? (dp_word >> (8 * ((kdig - 1) & 3))) & 0xFFu : 0u;
+        dig[kdig] = (int32_t)dk + (int32_t)(dp >= 128u) - 256 * (int32_t)(dk >= 128u);
     }
     __syncthreads();
     // 8 shifted copies of the reversed digits as fp16: copy o, entry i = r[i + o]
