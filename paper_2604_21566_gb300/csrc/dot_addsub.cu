@@ -118,7 +118,9 @@ __device__ uint32_t lookback_carry(const LookbackArgs &lb, const unsigned long l
             j_hi -= 32;   // 32 propagating predecessors: keep walking back
             continue;
         }
-        // a nearer predecessor has not published yet: wait (bounded)
+        // a nearer predecessor has not published yet: wait (bounded); the
+        // first polls are tight (a predecessor of the same round publishes
+        // within a few hundred cycles), later ones back off
         uint64_t now = 0;
         if (lane == 0) now = globaltimer_ns();
         now = __shfl_sync(DOT_FULL, now, 0);
@@ -129,7 +131,7 @@ __device__ uint32_t lookback_carry(const LookbackArgs &lb, const unsigned long l
             if (lane == 0) record_status(lb.status, DOT_ETIMEOUT);
             return 0;
         }
-        __nanosleep(100);
+        if (now - t0 > 2000) __nanosleep(64);
     }
 }
 
@@ -246,14 +248,15 @@ addsub_tile_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint32_t *
 }
 
 // ============================ tiled kernel (2b): bulk-copy prefetch + look-back
-// Same tiles, tickets and look-back as above, for 16-byte aligned rows with
-// m % 4 == 0.  Each block keeps two tiles in flight: thread 0 takes the next
-// ticket as soon as the block has read the current tile out of shared memory
-// and starts that tile's operand copies (cp.async.bulk, completion counted on
-// an mbarrier), so HBM keeps streaming while the block waits in look-back.
-// A block processes its tickets in the order it took them, so the lowest
-// unfinished ticket always belongs to a block that is processing it (not
-// prefetching it) and whose predecessors are done: the waits still end.
+// Same tiles and look-back as above, for 16-byte aligned rows with m % 4 == 0,
+// on a static round-robin schedule: block b takes tiles b, b + G, b + 2G, ...
+// (G blocks, all resident: a cooperative launch).  Each block keeps two tiles
+// in flight: as soon as it has read tile k out of shared memory, thread 0
+// starts the operand copies of tile k + 2 (cp.async.bulk, completion counted
+// on an mbarrier), so HBM keeps streaming while the block waits in look-back.
+// A tile's predecessor belongs to the previous block in the same round (or to
+// the last block one round earlier), which is processing it now: the waits
+// are short and always end, and no block holds a ticket it cannot start.
 template <bool SUB, int NCH>
 __global__ void __launch_bounds__(DOT_TILE_THREADS)
 addsub_tile_bulk_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint32_t *cout,
@@ -272,8 +275,8 @@ addsub_tile_bulk_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint3
     const unsigned long long epoch = lb.counters[2];
     const unsigned long long total = (unsigned long long)batch * tiles_per_op;
 
-    auto issue = [&](int st) {   // thread 0: take a ticket and start its copies
-        const unsigned long long tk = atomicAdd(&lb.counters[0], 1ull);
+    auto issue = [&](int st, int k) {   // thread 0: start the copies of this block's k-th tile
+        const unsigned long long tk = blockIdx.x + (unsigned long long)k * gridDim.x;
         s_ticket[st] = tk;
         if (tk < total) {
             const unsigned long long op = tk / tiles_per_op, t = tk - op * tiles_per_op;
@@ -289,8 +292,8 @@ addsub_tile_bulk_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint3
         mbar_init(&s_bar[0], 1);
         mbar_init(&s_bar[1], 1);
         mbar_init_fence();
-        issue(0);
-        issue(1);
+        issue(0, 0);
+        issue(1, 1);
     }
     __syncthreads();
 
@@ -335,7 +338,7 @@ addsub_tile_bulk_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint3
         }
         if (lane == 0) s_wagg[st][warp] = wg | (wp << 1);
         __syncthreads();   // stage st fully read; warp aggregates visible
-        if (threadIdx.x == 0) issue(st);
+        if (threadIdx.x == 0) issue(st, k + 2);
 
         if (warp == 0) {
             uint32_t tg = 0, tp = 1;
@@ -473,15 +476,13 @@ static dot_status_t launch_tile(dot_ctx_t ctx, const dot_plan_t &pl, const uint3
                                         : (const void *)addsub_tile_bulk_kernel<SUB, 4>;
         if (cudaFuncSetAttribute(fb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return DOT_ECUDA;
+        // every block resident at once (the static schedule's look-back relies on it)
         const size_t cap = (size_t)ctx->num_sms * dot_blocks_per_sm(fb, DOT_TILE_THREADS, smem);
         const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
-        if (pl.chunks == 1)
-            addsub_tile_bulk_kernel<SUB, 1><<<grid, DOT_TILE_THREADS, smem, st>>>(a, b, s, cout, m, batch, tpo, lb);
-        else if (pl.chunks == 2)
-            addsub_tile_bulk_kernel<SUB, 2><<<grid, DOT_TILE_THREADS, smem, st>>>(a, b, s, cout, m, batch, tpo, lb);
-        else
-            addsub_tile_bulk_kernel<SUB, 4><<<grid, DOT_TILE_THREADS, smem, st>>>(a, b, s, cout, m, batch, tpo, lb);
-        return cudaGetLastError() == cudaSuccess ? DOT_OK : DOT_ECUDA;
+        void *args[] = {(void *)&a, (void *)&b, (void *)&s, (void *)&cout, (void *)&m, (void *)&batch,
+                        (void *)&tpo, (void *)&lb};
+        const cudaError_t e = cudaLaunchCooperativeKernel(fb, dim3(grid), dim3(DOT_TILE_THREADS), args, smem, st);
+        return e == cudaSuccess ? DOT_OK : DOT_ECUDA;
     }
     const void *fn;
     if (pl.chunks == 1) fn = (const void *)addsub_tile_kernel<SUB, SEG, 1>;
