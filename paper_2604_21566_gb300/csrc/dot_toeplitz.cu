@@ -245,42 +245,51 @@ __device__ __forceinline__ uint32_t tz_shifted2(uint32_t x, uint32_t sel)
 // --------------------------------------------------------------- kernel
 // Staging split in two: the next tile's limbs are loaded into registers early
 // (their latency hides behind the current tile's drain) and converted into the
-// fp16 tile once the tensor core is done with it.
+// fp16 k-block buffers once the tensor core is done with them.  Worker w holds
+// row w % 128's limbs 8q .. 8q + 7 of each k-block (q = w / 128), so that all
+// workers convert each k-block together: x[0..8) for k-block 0, x[8..16) for 1.
 __device__ __forceinline__ void tz_load(uint32_t (&x)[16], const uint32_t *b, int m, size_t batch, size_t tile, int w)
 {
-    const int row = w & (TZ_M - 1), qr = w >> 7;
+    const int row = w & (TZ_M - 1), q = w >> 7;
     const size_t op = tile * TZ_M + row;
-    const uint32_t *src = b + op * (size_t)m + 16 * qr;
+    const uint32_t *src = b + op * (size_t)m + 8 * q;
     if (op < batch && m == TZ_MAX_LIMBS && aligned16(src)) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(src) + q);
-            x[4 * q] = v.x; x[4 * q + 1] = v.y; x[4 * q + 2] = v.z; x[4 * q + 3] = v.w;
-        }
+        for (int kb = 0; kb < 2; ++kb)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(src + 32 * kb) + h);
+                x[8 * kb + 4 * h] = v.x; x[8 * kb + 4 * h + 1] = v.y;
+                x[8 * kb + 4 * h + 2] = v.z; x[8 * kb + 4 * h + 3] = v.w;
+            }
     } else {
 #pragma unroll
-        for (int l = 0; l < 16; ++l) x[l] = (op < batch && 16 * qr + l < m) ? __ldcs(src + l) : 0u;
+        for (int l = 0; l < 16; ++l) {
+            const int limb = 32 * (l >> 3) + 8 * q + (l & 7);
+            x[l] = (op < batch && limb < m) ? __ldcs(b + op * (size_t)m + limb) : 0u;
+        }
     }
 }
 
 // Digits beyond the operand's 4m enter as 0 (not -128), so that every batch
 // row has exactly the digit window that the limb constants assume.  Worker w
-// converts row w % 128, digits 64 (w / 128) .. + 63, i.e. half of k-block
-// (w / 256), into that k-block's buffer kbuf.
-__device__ __forceinline__ void tz_convert(unsigned char *kbuf, const uint32_t (&x)[16], int w, int m)
+// converts row w % 128's limbs 8q .. 8q + 7 of k-block kb (q = w / 128):
+// digits 32q .. 32q + 31 of the k-block, into its buffer kbuf.
+__device__ __forceinline__ void tz_convert(unsigned char *kbuf, const uint32_t (&x)[16], int kb, int w, int m)
 {
-    const int row = w & (TZ_M - 1), qr = w >> 7;
-    const bool full = 16 * qr + 16 <= m;
+    const int row = w & (TZ_M - 1), q = w >> 7;
+    const int limb0 = 32 * kb + 8 * q;   // first limb of the operand held here
+    const bool full = limb0 + 8 <= m;
 #pragma unroll
-    for (int l2 = 0; l2 < 8; ++l2) {
-        const uint32_t x0 = x[2 * l2], x1 = x[2 * l2 + 1];
+    for (int l2 = 0; l2 < 4; ++l2) {
+        const uint32_t x0 = x[8 * kb + 2 * l2], x1 = x[8 * kb + 2 * l2 + 1];
         uint4 v = make_uint4(tz_shifted2(x0, 0x4140), tz_shifted2(x0, 0x4342), tz_shifted2(x1, 0x4140),
                              tz_shifted2(x1, 0x4342));
         if (!full) {
-            if (16 * qr + 2 * l2 >= m) v.x = v.y = 0u;
-            if (16 * qr + 2 * l2 + 1 >= m) v.z = v.w = 0u;
+            if (limb0 + 2 * l2 >= m) v.x = v.y = 0u;
+            if (limb0 + 2 * l2 + 1 >= m) v.z = v.w = 0u;
         }
-        *reinterpret_cast<uint4 *>(kbuf + tz_off(row, 64 * (qr & 1) + 8 * l2, TZ_M)) = v;
+        *reinterpret_cast<uint4 *>(kbuf + tz_off(row, 32 * q + 8 * l2, TZ_M)) = v;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -626,8 +635,8 @@ toeplitz_mma_kernel(const uint32_t *fixed, const uint32_t *b, uint32_t *p, int m
                      :: "r"(smem_u32(tmem_slot)), "r"(512) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
         if (lane == 0) {
-            mbar_init(bar_staged + 0, TZ_WORKERS / 64);   // arrivals per warp
-            mbar_init(bar_staged + 1, TZ_WORKERS / 64);
+            mbar_init(bar_staged + 0, TZ_WORKERS / 32);   // arrivals per warp
+            mbar_init(bar_staged + 1, TZ_WORKERS / 32);
             mbar_init(bar_kb1done, 1);
             mbar_init(bar_full + 0, 1);
             mbar_init(bar_full + 1, 1);
@@ -735,10 +744,11 @@ toeplitz_mma_kernel(const uint32_t *fixed, const uint32_t *b, uint32_t *p, int m
     } else {
         const int quad = warp & 3, seg = warp >> 2;   // TMEM lane quadrant, 16-limb segment
         int late = 0;
-        const int kb = tid >> 8;   // the k-block this worker stages
         if (blockIdx.x < ntiles) {
-            tz_convert(tz_kbuf(sA, kb, 0), x, tid, m);
-            tz_warp_arrive(bar_staged + kb);
+            for (int kb = 0; kb < 2; ++kb) {
+                tz_convert(tz_kbuf(sA, kb, 0), x, kb, tid, m);
+                tz_warp_arrive(bar_staged + kb);
+            }
         }
         int it = 0;
         for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
@@ -754,9 +764,9 @@ toeplitz_mma_kernel(const uint32_t *fixed, const uint32_t *b, uint32_t *p, int m
             // of the half-0 epilogue), its k-block 1 into this tile's k-block 0
             // buffer once the whole tile is done
             auto stage_kb0 = [&](int &lt) {
-                if (kb == 0 && next < ntiles) {
+                if (next < ntiles) {
                     lt |= !mbar_wait_bounded(bar_kb1done, ph, wait_ns);
-                    tz_convert(tz_kbuf(sA, 0, it + 1), x, tid, m);
+                    tz_convert(tz_kbuf(sA, 0, it + 1), x, 0, tid, m);
                     tz_warp_arrive(bar_staged + 0);
                 }
             };
@@ -765,8 +775,8 @@ toeplitz_mma_kernel(const uint32_t *fixed, const uint32_t *b, uint32_t *p, int m
                                        late_out, status, wait_ns);
             late = late_out;
             late |= !mbar_wait_bounded(bar_full + 1, ph, wait_ns);
-            if (kb == 1 && next < ntiles) {
-                tz_convert(tz_kbuf(sA, 1, it + 1), x, tid, m);
+            if (next < ntiles) {
+                tz_convert(tz_kbuf(sA, 1, it + 1), x, 1, tid, m);
                 tz_warp_arrive(bar_staged + 1);
             }
             tz_fence_after();
