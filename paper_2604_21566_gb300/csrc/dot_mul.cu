@@ -7,7 +7,9 @@
 //  * Column sums (Alg. 2 Phases 1-4).  Thread t of an op's group owns two
 //    blocks of R consecutive columns, [tR, tR+R) and [m' + tR, m' + tR + R)
 //    (m' = m rounded up to R), so every thread does the same m' R products:
-//    column c has c+1 pairs and column m'+c has m'-1-c.  For each i it forms
+//    column c has c+1 pairs and column m'+c has m'-1-c.  Both blocks run in
+//    one loop over row groups (low block first), so no lane of a warp idles
+//    while another finishes a longer block.  For each i it forms
 //    the R products A_i * B_{c-i} of its block independently (low and high
 //    halves: 2 multiplies on the FMA pipe) and adds each into its column's
 //    three-word sum (3 adds on the ALU pipe, in parallel with the next
@@ -27,7 +29,7 @@
 #include "dot_mul.cuh"
 
 // smallest operand (limbs) squared with the symmetric column sums
-#define DOT_SQR_MIN_LIMBS 64
+#define DOT_SQR_MIN_LIMBS 128
 
 // Batched product: runs of T = m'/R lanes, 32/T ops per warp.  SQR: the
 // square of a (b is a), with half the partial products.
@@ -194,9 +196,10 @@ DOT_API dot_status_t dot_sqr(dot_ctx_t ctx, const uint32_t *a, uint32_t *p, size
     rc = dot_make_plan(DOT_OP_MUL, m, batch, true, &pl, ctx->tune[DOT_OP_MUL][dot_tune_bucket(m)]);
     if (rc != DOT_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    // Below 64 limbs the rows near the diagonal, summed one column at a time,
-    // cost about what the halving saves (measured: 0.95x at m = 32, 1.42x at
-    // m = 128, 1.61x at m = 256), so small squares take the general product.
+    // Below 128 limbs the rows near the diagonal, summed one column at a time,
+    // cost about what the halving saves (measured against the general
+    // product: 0.95x at m = 64, 1.21x at m = 128, 1.46x at m = 256), so small
+    // squares take the general product.
     const bool sym = m >= DOT_SQR_MIN_LIMBS;
     switch (pl.seg_limbs) {
     case 4: return sym ? launch_mul_batched<4, true>(ctx, pl, a, a, p, m, batch, st)

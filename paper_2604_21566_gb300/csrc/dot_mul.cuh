@@ -5,10 +5,11 @@
 #include "dot_internal.cuh"
 
 #define MUL_WARPS 4
-// Resident blocks per SM the compiler must allow (caps registers per thread):
-// 6 blocks of 4 warps fit R <= 8 in 80 registers without spills; R = 16
-// needs its ~170 registers.
-__host__ __device__ constexpr int dot_mul_min_blocks(int R) { return R <= 8 ? 6 : 1; }
+// Resident blocks per SM the compiler must allow (caps registers per thread).
+// Both blocks' sums stay live through the row loop (colsum_pair): R = 8 fits
+// 4 blocks of 4 warps (128 registers), R = 4 fits 6 (80 registers; the
+// smallest products need the occupancy more), R = 16 needs ~170-190.
+__host__ __device__ constexpr int dot_mul_min_blocks(int R) { return R <= 4 ? 6 : (R <= 8 ? 4 : 1); }
 
 // Column sums of one block of R columns, kept as three 32-bit words each:
 // S_k = s2[k] X^2 + s1[k] X + s0[k]  (S_k < m 2^64 needs 64 + log2 m bits).
@@ -60,36 +61,59 @@ __device__ __forceinline__ void lds_vec(const uint32_t *p, uint32_t *v)
     }
 }
 
-// Positional sum W = sum_{k<R} S_{c0+k} X^k of the block of columns [c0, c0+R),
+// Positional sums W = sum_{k<R} S_{c0+k} X^k of both column blocks of lane t,
+// the low one [tR, tR + R) and the high one [m' + tR, m' + tR + R), with
 // S_c = sum_{i+j=c} A_i B_j.  As = A[0..m'), Bs = B[-R .. m'+R) (zeros outside
-// [0, m)), both in shared memory.  For row i the block needs B[c0 + k - i],
+// [0, m)), both in shared memory.  For row i a block needs B[c0 + k - i],
 // k < R: a window of R values that slides down by one per row, so each row
 // reads A_i (a broadcast) and one new B value; rows are unrolled R at a time
-// so the slide is register renaming.
+// so the slide is register renaming.  Both blocks run in ONE loop of T + 1
+// row groups (T = m'/R lanes per op).  The low block needs row groups 0 .. t and the high block t .. T-1, so
+// every lane runs the same T + 1 groups; summing the two blocks one after the
+// other would instead keep the warp busy for 2T groups with, on average, half
+// its lanes idle (lane t's low block is short where its high block is long).
+// At the switch the running sums are copied aside and the window restarts for
+// the high block; the high block's sums are the final sums minus the copy.
 template <int R>
-__device__ __forceinline__ void colsum_block(const uint32_t *As, const uint32_t *Bs, int c0, int mp,
-                                             uint32_t (&W)[R + 2])
+__device__ __forceinline__ void colsum_pair(const uint32_t *As, const uint32_t *Bs, int t, int T, int mp,
+                                            uint32_t (&Wl)[R + 2], uint32_t (&Wh)[R + 2])
 {
-    uint32_t s0[R], s1[R], s2[R];
+    uint32_t s0[R], s1[R], s2[R], l0[R], l1[R], l2[R];
 #pragma unroll
-    for (int k = 0; k < R; ++k) s0[k] = s1[k] = s2[k] = 0;
-    const int i_lo = max(0, c0 - mp + 1);
-    const int i_hi = min(c0 + R - 1, mp - 1);
-    int i0 = (i_lo / R) * R;
-    if (i0 <= i_hi) {
-        uint32_t w[R];
-        lds_vec<R>(Bs + R + (c0 - i0), w);   // w[k] = B[c0 + k - i0]
-        for (; i0 <= i_hi; i0 += R) {
+    for (int k = 0; k < R; ++k) s0[k] = s1[k] = s2[k] = l0[k] = l1[k] = l2[k] = 0;
+    uint32_t w[R];
+    lds_vec<R>(Bs + R + t * R, w);   // w[k] = B[tR + k]: the low block at row 0
+    int cb = t * R;                  // first column of the current block
+    int i0 = 0;                      // first row of the current group
+    for (int g = 0; g <= T; ++g) {
+        if (g == t + 1) {
 #pragma unroll
-            for (int ii = 0; ii < R; ++ii) {
-                mac_cols<R>(s0, s1, s2, As[i0 + ii], w);
-#pragma unroll
-                for (int k = R - 1; k > 0; --k) w[k] = w[k - 1];
-                w[0] = Bs[R + c0 - (i0 + ii) - 1];
+            for (int k = 0; k < R; ++k) {
+                l0[k] = s0[k];
+                l1[k] = s1[k];
+                l2[k] = s2[k];
             }
+            cb = mp + t * R;
+            i0 = t * R;
+            lds_vec<R>(Bs + R + mp, w);   // w[k] = B[cb + k - i0] = B[m' + k] (zero padding)
         }
+#pragma unroll
+        for (int ii = 0; ii < R; ++ii) {
+            mac_cols<R>(s0, s1, s2, As[i0 + ii], w);
+#pragma unroll
+            for (int k = R - 1; k > 0; --k) w[k] = w[k - 1];
+            w[0] = Bs[R + cb - (i0 + ii) - 1];
+        }
+        i0 += R;
     }
-    cols_to_positional<R>(s0, s1, s2, W);
+    // high sums = final - low (three-word subtraction per column; never negative)
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+        asm("sub.cc.u32 %0, %0, %3;\n\tsubc.cc.u32 %1, %1, %4;\n\tsubc.u32 %2, %2, %5;"
+            : "+r"(s0[k]), "+r"(s1[k]), "+r"(s2[k])
+            : "r"(l0[k]), "r"(l1[k]), "r"(l2[k]));
+    cols_to_positional<R>(l0, l1, l2, Wl);
+    cols_to_positional<R>(s0, s1, s2, Wh);
 }
 
 // One column: (s2:s1:s0) += a * w
@@ -109,31 +133,14 @@ __device__ __forceinline__ void mac1(uint32_t &s0, uint32_t &s1, uint32_t &s2, u
 // S_c = 2 sum_{i<j, i+j=c} A_i A_j + [c even] A_{c/2}^2, so only rows with
 // 2i < c are summed (about half of them), doubled, and the diagonal square
 // added.  Rows with 2i < c0 feed every column of the block and use the
-// sliding window; the few rows with c0 <= 2i < c0 + R feed only the columns
-// c > 2i and are summed one column at a time.
+// sliding window (sqr_colsum_pair); the few rows with c0 <= 2i < c0 + R feed
+// only the columns c > 2i and are summed one column at a time here, from row
+// i0 (the first row the window did not take) on.
 template <int R>
-__device__ __forceinline__ void sqr_colsum_block(const uint32_t *As, const uint32_t *Bs, int c0, int mp,
-                                                 uint32_t (&W)[R + 2])
+__device__ __forceinline__ void sqr_block_tail(const uint32_t *As, const uint32_t *Bs, int c0, int mp, int i0,
+                                               uint32_t (&s0)[R], uint32_t (&s1)[R], uint32_t (&s2)[R],
+                                               uint32_t (&W)[R + 2])
 {
-    uint32_t s0[R], s1[R], s2[R];
-#pragma unroll
-    for (int k = 0; k < R; ++k) s0[k] = s1[k] = s2[k] = 0;
-    const int i_lo = max(0, c0 - mp + 1);
-    const int i_full = min((c0 - 1) >> 1, mp - 1);   // last row with 2i < c0 (-1: none)
-    int i0 = (i_lo / R) * R;
-    if (i0 + R - 1 <= i_full) {
-        uint32_t w[R];
-        lds_vec<R>(Bs + R + (c0 - i0), w);   // w[k] = A[c0 + k - i0]
-        for (; i0 + R - 1 <= i_full; i0 += R) {
-#pragma unroll
-            for (int ii = 0; ii < R; ++ii) {
-                mac_cols<R>(s0, s1, s2, As[i0 + ii], w);
-#pragma unroll
-                for (int k = R - 1; k > 0; --k) w[k] = w[k - 1];
-                w[0] = Bs[R + c0 - (i0 + ii) - 1];
-            }
-        }
-    }
     const int i_top = min((c0 + R - 1) >> 1, mp - 1);   // last row with 2i < c0 + R
     for (int i = i0; i <= i_top; ++i) {
         const uint32_t ai = As[i];
@@ -154,6 +161,56 @@ __device__ __forceinline__ void sqr_colsum_block(const uint32_t *As, const uint3
         mac1(s0[k], s1[k], s2[k], d, d);
     }
     cols_to_positional<R>(s0, s1, s2, W);
+}
+
+// Both blocks of lane t for a square, as colsum_pair: the low block takes the
+// row groups that lie wholly below the diagonal of [tR, tR + R) (rows from 0),
+// the high block those of [m' + tR, ...) (rows from tR); the two counts add up
+// to about T/2 for every lane, so one loop covers both with (at most) one
+// group of imbalance.  Each block's near-diagonal rows follow the loop.
+template <int R>
+__device__ __forceinline__ void sqr_colsum_pair(const uint32_t *As, const uint32_t *Bs, int t, int mp,
+                                                uint32_t (&Wl)[R + 2], uint32_t (&Wh)[R + 2])
+{
+    const int cl = t * R, ch = mp + t * R;
+    // full groups: rows i < c0 / 2 for every column of the block
+    const int n_lo = (((cl - 1) >> 1) + 1) / R;        // from row 0
+    const int n_hi = (((ch - 1) >> 1) + 1 - cl) / R;   // from row tR
+    uint32_t s0[R], s1[R], s2[R], l0[R], l1[R], l2[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) s0[k] = s1[k] = s2[k] = l0[k] = l1[k] = l2[k] = 0;
+    uint32_t w[R];
+    lds_vec<R>(Bs + R + cl, w);   // w[k] = A[tR + k]: the low block at row 0
+    int cb = cl, i0 = 0;
+    for (int g = 0;; ++g) {
+        if (g == n_lo) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                l0[k] = s0[k];
+                l1[k] = s1[k];
+                l2[k] = s2[k];
+            }
+            cb = ch;
+            i0 = cl;
+            lds_vec<R>(Bs + R + mp, w);   // w[k] = A[ch + k - tR] = A[m' + k] (zero padding)
+        }
+        if (g == n_lo + n_hi) break;
+#pragma unroll
+        for (int ii = 0; ii < R; ++ii) {
+            mac_cols<R>(s0, s1, s2, As[i0 + ii], w);
+#pragma unroll
+            for (int k = R - 1; k > 0; --k) w[k] = w[k - 1];
+            w[0] = Bs[R + cb - (i0 + ii) - 1];
+        }
+        i0 += R;
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+        asm("sub.cc.u32 %0, %0, %3;\n\tsubc.cc.u32 %1, %1, %4;\n\tsubc.u32 %2, %2, %5;"
+            : "+r"(s0[k]), "+r"(s1[k]), "+r"(s2[k])
+            : "r"(l0[k]), "r"(l1[k]), "r"(l2[k]));
+    sqr_block_tail<R>(As, Bs, cl, mp, n_lo * R, l0, l1, l2, Wl);
+    sqr_block_tail<R>(As, Bs, ch, mp, cl + n_hi * R, s0, s1, s2, Wh);
 }
 
 // Copy limbs [t R, t R + R) of an m-limb row into shared memory (zeros past m).
@@ -199,16 +256,17 @@ __device__ __forceinline__ void mul_group(const uint32_t *As, const uint32_t *Bs
     const int lane = (int)lane_id();
     on = on && t < tn;
     const int last = min(grp * T + max(tn, 1) - 1, 31);
-    uint32_t W[R + 2];
+    uint32_t W[R + 2], WH[R + 2];
     uint32_t wl, wh, mid;
-    {   // low blocks [tR, tR + R): positions 0 .. m' - 1
-        if (on) {
-            if (SQR) sqr_colsum_block<R>(As, Bs, t * R, mp, W);
-            else colsum_block<R>(As, Bs, t * R, mp, W);
-        } else {
+    // both blocks in one pass (the lanes t < tn of a run take the same row groups)
+    if (on) {
+        if (SQR) sqr_colsum_pair<R>(As, Bs, t, mp, W, WH);
+        else colsum_pair<R>(As, Bs, t, tn, mp, W, WH);
+    } else {
 #pragma unroll
-            for (int k = 0; k < R + 2; ++k) W[k] = 0;
-        }
+        for (int k = 0; k < R + 2; ++k) W[k] = WH[k] = 0;
+    }
+    {   // low blocks [tR, tR + R): positions 0 .. m' - 1
         // the two overflow words of each block belong to the next block
         const uint32_t ul = __shfl_up_sync(DOT_FULL, W[R], 1), uh = __shfl_up_sync(DOT_FULL, W[R + 1], 1);
         wl = __shfl_sync(DOT_FULL, W[R], last);   // top low block -> first high block
@@ -230,13 +288,8 @@ __device__ __forceinline__ void mul_group(const uint32_t *As, const uint32_t *Bs
         if (on) store_block<R>(prow, t * R, 2 * m, sg.r, vec_out);
     }
     {   // high blocks [m' + tR, m' + tR + R)
-        if (on) {
-            if (SQR) sqr_colsum_block<R>(As, Bs, mp + t * R, mp, W);
-            else colsum_block<R>(As, Bs, mp + t * R, mp, W);
-        } else {
 #pragma unroll
-            for (int k = 0; k < R + 2; ++k) W[k] = 0;
-        }
+        for (int k = 0; k < R + 2; ++k) W[k] = WH[k];
         const uint32_t ul = __shfl_up_sync(DOT_FULL, W[R], 1), uh = __shfl_up_sync(DOT_FULL, W[R + 1], 1);
         uint32_t l[R], h[R];
 #pragma unroll
