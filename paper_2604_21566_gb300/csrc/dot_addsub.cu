@@ -94,6 +94,22 @@ addsub_warp_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint32_t *
 // ends.  Each tile publishes its carry state (epoch-tagged): INCLUSIVE as soon
 // as its own aggregate decides the carry-out (generate or kill), PROPAGATE
 // otherwise, then INCLUSIVE once its carry-in is known.
+// A tile state is one self-contained word (epoch and carry code): its reader
+// needs nothing else the writer stored, so relaxed gpu-scope accesses are
+// enough.  A release store would hold each publication until every earlier
+// store of the block (the previous tile's sums) had drained to L2.
+__device__ __forceinline__ unsigned long long ld_state(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_state(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
+}
+
 __device__ uint32_t lookback_carry(const LookbackArgs &lb, const unsigned long long *st_op,
                                    long long t, unsigned long long epoch, int lane)
 {
@@ -104,7 +120,7 @@ __device__ uint32_t lookback_carry(const LookbackArgs &lb, const unsigned long l
         const long long j = j_hi - lane;
         uint32_t code = LB_INCL0;   // before the op's first tile: carry 0
         if (j >= 0) {
-            const unsigned long long w = ld_acquire_u64(st_op + j);
+            const unsigned long long w = ld_state(st_op + j);
             code = ((w >> 2) == epoch) ? (uint32_t)(w & 3ull) : (uint32_t)LB_EMPTY;
         }
         const uint32_t incl = __ballot_sync(DOT_FULL, code >= LB_INCL0);
@@ -201,13 +217,13 @@ addsub_tile_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint32_t *
             uint32_t cin_tile = 0;
             if (t == 0) {
                 if (lane == 0 && !skip)
-                    st_release_u64(st_op, (epoch << 2) | (tg ? LB_INCL1 : LB_INCL0));
+                    st_state(st_op, (epoch << 2) | (tg ? LB_INCL1 : LB_INCL0));
             } else {
                 if (lane == 0 && !skip)
-                    st_release_u64(st_op + t, (epoch << 2) | (tp ? LB_PROP : (tg ? LB_INCL1 : LB_INCL0)));
+                    st_state(st_op + t, (epoch << 2) | (tp ? LB_PROP : (tg ? LB_INCL1 : LB_INCL0)));
                 cin_tile = lookback_carry(lb, st_op, (long long)t, epoch, lane);
                 if (tp && lane == 0 && !skip)
-                    st_release_u64(st_op + t, (epoch << 2) | (cin_tile ? LB_INCL1 : LB_INCL0));
+                    st_state(st_op + t, (epoch << 2) | (cin_tile ? LB_INCL1 : LB_INCL0));
             }
             if (lane == 0) s_cin = cin_tile;
         }
@@ -250,26 +266,95 @@ addsub_tile_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint32_t *
 // ============================ tiled kernel (2b): bulk-copy prefetch + look-back
 // Same tiles and look-back as above, for 16-byte aligned rows with m % 4 == 0,
 // on a static round-robin schedule: block b takes tiles b, b + G, b + 2G, ...
-// (G blocks, all resident: a cooperative launch).  Each block keeps two tiles
-// in flight: as soon as it has read tile k out of shared memory, thread 0
-// starts the operand copies of tile k + 2 (cp.async.bulk, completion counted
-// on an mbarrier), so HBM keeps streaming while the block waits in look-back.
+// (G blocks, all resident: a cooperative launch).  Each block streams its
+// tiles through two shared-memory stages (cp.async.bulk, completion counted on
+// an mbarrier) and works one tile AHEAD: as soon as tile k + 1 has arrived it
+// forms and publishes that tile's aggregate, and only then resolves tile k's
+// carry-in and stores tile k.  A tile's predecessor therefore has almost always
+// published a round earlier, and the look-back wait leaves the critical path;
+// publishing only after the previous tile was stored made every block wait on
+// its predecessor's progress, and the delays travelled along each op's tiles.
 // A tile's predecessor belongs to the previous block in the same round (or to
-// the last block one round earlier), which is processing it now: the waits
-// are short and always end, and no block holds a ticket it cannot start.
+// the last block one round earlier); all blocks are resident and publish in
+// ticket order within a block, so the waits always end.
 template <bool SUB, int NCH>
-__global__ void __launch_bounds__(DOT_TILE_THREADS)
+struct TileRegs {
+    Segment<SUB, 4> sg[NCH];
+    uint32_t G[NCH], P[NCH];
+};
+
+template <bool SUB, int NCH>
+__device__ __forceinline__ void tile_bulk_aggregate(const uint32_t *stage, unsigned long long ticket,
+                                                    unsigned long long tiles_per_op, size_t m, int st,
+                                                    TileRegs<SUB, NCH> &tr, uint32_t (&s_wagg)[2][DOT_TILE_THREADS / 32],
+                                                    int lane, int warp)
+{
+    constexpr unsigned long long TILE = (unsigned long long)DOT_TILE_THREADS * 4 * NCH;
+    constexpr int WARP_LIMBS = 32 * 4 * NCH;
+    const unsigned long long t = ticket % tiles_per_op;
+    const size_t wbase = (size_t)(t * TILE) + (size_t)warp * WARP_LIMBS;
+    const uint32_t *xa = stage + (2 * st) * TILE + warp * WARP_LIMBS;
+    const uint32_t *xb = stage + (2 * st + 1) * TILE + warp * WARP_LIMBS;
+    uint32_t wg = 0, wp = 1;
+#pragma unroll
+    for (int j = 0; j < NCH; ++j) {
+        const size_t li = wbase + ((size_t)j * 32 + lane) * 4;
+        const bool on = li < m;
+        uint32_t x[4] = {0u, 0u, 0u, 0u}, y[4] = {0u, 0u, 0u, 0u};
+        if (on) {
+            const uint4 qa = reinterpret_cast<const uint4 *>(xa)[j * 32 + lane];
+            const uint4 qb = reinterpret_cast<const uint4 *>(xb)[j * 32 + lane];
+            x[0] = qa.x; x[1] = qa.y; x[2] = qa.z; x[3] = qa.w;
+            y[0] = qb.x; y[1] = qb.y; y[2] = qb.z; y[3] = qb.w;
+        }
+        tr.sg[j].phase12(x, y);
+        WarpCarry wc;
+        wc.resolve(on ? tr.sg[j].g() : 0u, on ? tr.sg[j].p() : 0u, 0u, 1u, 0x80000000u);
+        tr.G[j] = wc.G;
+        tr.P[j] = wc.P;
+        gp_compose(wg, wp, wc.carry_out(31), (uint32_t)(wc.P == DOT_FULL));
+    }
+    if (lane == 0) s_wagg[st][warp] = wg | (wp << 1);
+}
+
+template <bool SUB, int NCH>
+__device__ __forceinline__ void tile_bulk_apply(TileRegs<SUB, NCH> &tr, uint32_t *s, uint32_t *cout,
+                                                unsigned long long ticket, unsigned long long tiles_per_op,
+                                                size_t m, uint32_t c, int lane, int warp)
+{
+    constexpr unsigned long long TILE = (unsigned long long)DOT_TILE_THREADS * 4 * NCH;
+    constexpr int WARP_LIMBS = 32 * 4 * NCH;
+    const unsigned long long op = ticket / tiles_per_op;
+    const unsigned long long t = ticket - op * tiles_per_op;
+    const size_t wbase = (size_t)(t * TILE) + (size_t)warp * WARP_LIMBS;
+    uint32_t *sr = s + op * m;
+#pragma unroll
+    for (int j = 0; j < NCH; ++j) {
+        const size_t li = wbase + ((size_t)j * 32 + lane) * 4;
+        const uint32_t Pm = tr.P[j] & 0x7fffffffu;
+        const uint32_t C = (((tr.G[j] << 1) | c) + Pm) ^ Pm;
+        const uint32_t ci = (C >> lane) & 1u;
+        tr.sg[j].apply(ci);
+        if (li < m) {
+            store_seg<4>(sr + li, tr.sg[j].r);
+            if (li + 4 >= m && t == tiles_per_op - 1) cout[op] = tr.sg[j].cout(ci);
+        }
+        c = ((tr.G[j] >> 31) | ((tr.P[j] >> 31) & (C >> 31))) & 1u;
+    }
+}
+
+template <bool SUB, int NCH>
+__global__ void __launch_bounds__(DOT_TILE_THREADS, 3)
 addsub_tile_bulk_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint32_t *cout,
                         size_t m, size_t batch, unsigned long long tiles_per_op, LookbackArgs lb)
 {
     constexpr int WARPS = DOT_TILE_THREADS / 32;
     constexpr unsigned long long TILE = (unsigned long long)DOT_TILE_THREADS * 4 * NCH;
-    constexpr int WARP_LIMBS = 32 * 4 * NCH;
     extern __shared__ __align__(128) uint32_t stage[];   // [2][2][TILE]: stage, operand
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ unsigned long long s_ticket[2];
     __shared__ uint32_t s_wagg[2][WARPS];
-    __shared__ uint32_t s_cin[2];
+    __shared__ uint32_t s_cin;
     const int lane = (int)lane_id();
     const int warp = (int)(threadIdx.x >> 5);
     const unsigned long long epoch = lb.counters[2];
@@ -288,6 +373,57 @@ addsub_tile_bulk_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint3
             bulk_g2s(stage + (2 * st + 1) * TILE, b + op * m + first, bytes, &s_bar[st]);
         }
     };
+    // warp 0: compose the block aggregate of the tile in stage st and publish
+    // it (INCLUSIVE when it decides the carry-out, PROPAGATE otherwise)
+    auto publish = [&](int st, unsigned long long ticket) {
+        uint32_t tg = 0, tp = 1;
+#pragma unroll
+        for (int w = 0; w < WARPS; ++w) gp_compose(tg, tp, s_wagg[st][w] & 1u, s_wagg[st][w] >> 1);
+        const unsigned long long op = ticket / tiles_per_op, t = ticket - op * tiles_per_op;
+        const bool skip = lb.skip_tile >= 0 && op == 0 && (long long)t == lb.skip_tile;
+        if (lane == 0 && !skip)
+            st_state(lb.state + ticket, (epoch << 2) | ((tp && t > 0) ? LB_PROP : (tg ? LB_INCL1 : LB_INCL0)));
+    };
+    // all threads: wait for the tile of stage st, form its aggregates, publish,
+    // and reuse the stage for the tile two ahead
+    auto take = [&](int st, int k, TileRegs<SUB, NCH> &tr) {
+        if (!mbar_wait_bounded(&s_bar[st], (uint32_t)((k >> 1) & 1), lb.wait_limit_ns) && lane == 0)
+            record_status(lb.status, DOT_ETIMEOUT);
+        tile_bulk_aggregate<SUB, NCH>(stage, s_ticket[st], tiles_per_op, m, st, tr, s_wagg, lane, warp);
+        __syncthreads();   // stage st fully read; warp aggregates visible
+        const unsigned long long ticket = s_ticket[st];
+        if (warp == 0) publish(st, ticket);
+        __syncthreads();   // every thread has read s_ticket[st] before it is rewritten
+        if (threadIdx.x == 0) issue(st, k + 2);
+    };
+    // warp 0: carry into the tile of stage st (the look-back; a PROPAGATE tile
+    // then publishes INCLUSIVE); all threads: add it in and store the tile
+    auto finish = [&](int st, unsigned long long ticket, TileRegs<SUB, NCH> &tr) {
+        if (warp == 0) {
+            const unsigned long long op = ticket / tiles_per_op, t = ticket - op * tiles_per_op;
+            uint32_t cin_tile = 0;
+            if (t > 0) {
+                const unsigned long long *st_op = lb.state + (ticket - t);
+                uint32_t tg = 0, tp = 1;
+#pragma unroll
+                for (int w = 0; w < WARPS; ++w) gp_compose(tg, tp, s_wagg[st][w] & 1u, s_wagg[st][w] >> 1);
+                cin_tile = lookback_carry(lb, st_op, (long long)t, epoch, lane);
+                const bool skip = lb.skip_tile >= 0 && op == 0 && (long long)t == lb.skip_tile;
+                if (tp && lane == 0 && !skip)
+                    st_state(lb.state + ticket, (epoch << 2) | (cin_tile ? LB_INCL1 : LB_INCL0));
+            }
+            if (lane == 0) s_cin = cin_tile;
+        }
+        __syncthreads();
+        uint32_t c = s_cin;
+        for (int w = 0; w < warp; ++w) {
+            const uint32_t g = s_wagg[st][w] & 1u, p = s_wagg[st][w] >> 1;
+            c = g | (p & c);
+        }
+        tile_bulk_apply<SUB, NCH>(tr, s, cout, ticket, tiles_per_op, m, c, lane, warp);
+        __syncthreads();   // s_cin and s_wagg[st] are read before they are rewritten
+    };
+
     if (threadIdx.x == 0) {
         mbar_init(&s_bar[0], 1);
         mbar_init(&s_bar[1], 1);
@@ -297,90 +433,22 @@ addsub_tile_bulk_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint3
     }
     __syncthreads();
 
-    for (int k = 0;; ++k) {
-        const int st = k & 1;
-        const unsigned long long ticket = s_ticket[st];
-        if (ticket >= total) break;
-        const unsigned long long op = ticket / tiles_per_op;
-        const unsigned long long t = ticket - op * tiles_per_op;
-        const size_t wbase = (size_t)(t * TILE) + (size_t)warp * WARP_LIMBS;
-        if (!mbar_wait_bounded(&s_bar[st], (uint32_t)((k >> 1) & 1), lb.wait_limit_ns) && lane == 0)
-            record_status(lb.status, DOT_ETIMEOUT);
-        const uint32_t *xa = stage + (2 * st) * TILE + warp * WARP_LIMBS;
-        const uint32_t *xb = stage + (2 * st + 1) * TILE + warp * WARP_LIMBS;
-        uint32_t x[NCH][4], y[NCH][4];
-#pragma unroll
-        for (int j = 0; j < NCH; ++j) {
-            const size_t li = wbase + ((size_t)j * 32 + lane) * 4;
-            if (li < m) {
-                const uint4 qa = reinterpret_cast<const uint4 *>(xa)[j * 32 + lane];
-                const uint4 qb = reinterpret_cast<const uint4 *>(xb)[j * 32 + lane];
-                x[j][0] = qa.x; x[j][1] = qa.y; x[j][2] = qa.z; x[j][3] = qa.w;
-                y[j][0] = qb.x; y[j][1] = qb.y; y[j][2] = qb.z; y[j][3] = qb.w;
-            } else {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) x[j][i] = y[j][i] = 0;
-            }
-        }
-        Segment<SUB, 4> sg[NCH];
-        uint32_t G[NCH], P[NCH];
-        uint32_t wg = 0, wp = 1;
-#pragma unroll
-        for (int j = 0; j < NCH; ++j) {
-            sg[j].phase12(x[j], y[j]);
-            const size_t li = wbase + ((size_t)j * 32 + lane) * 4;
-            const bool on = li < m;
-            WarpCarry wc;
-            wc.resolve(on ? sg[j].g() : 0u, on ? sg[j].p() : 0u, 0u, 1u, 0x80000000u);
-            G[j] = wc.G;
-            P[j] = wc.P;
-            gp_compose(wg, wp, wc.carry_out(31), (uint32_t)(wc.P == DOT_FULL));
-        }
-        if (lane == 0) s_wagg[st][warp] = wg | (wp << 1);
-        __syncthreads();   // stage st fully read; warp aggregates visible
-        if (threadIdx.x == 0) issue(st, k + 2);
-
-        if (warp == 0) {
-            uint32_t tg = 0, tp = 1;
-#pragma unroll
-            for (int w = 0; w < WARPS; ++w) gp_compose(tg, tp, s_wagg[st][w] & 1u, s_wagg[st][w] >> 1);
-            unsigned long long *st_op = lb.state + (ticket - t);
-            const bool skip = lb.skip_tile >= 0 && op == 0 && (long long)t == lb.skip_tile;
-            uint32_t cin_tile = 0;
-            if (t == 0) {
-                if (lane == 0 && !skip)
-                    st_release_u64(st_op, (epoch << 2) | (tg ? LB_INCL1 : LB_INCL0));
-            } else {
-                if (lane == 0 && !skip)
-                    st_release_u64(st_op + t, (epoch << 2) | (tp ? LB_PROP : (tg ? LB_INCL1 : LB_INCL0)));
-                cin_tile = lookback_carry(lb, st_op, (long long)t, epoch, lane);
-                if (tp && lane == 0 && !skip)
-                    st_release_u64(st_op + t, (epoch << 2) | (cin_tile ? LB_INCL1 : LB_INCL0));
-            }
-            if (lane == 0) s_cin[st] = cin_tile;
-        }
-        __syncthreads();
-
-        uint32_t c = s_cin[st];
-        for (int w = 0; w < warp; ++w) {
-            const uint32_t g = s_wagg[st][w] & 1u, p = s_wagg[st][w] >> 1;
-            c = g | (p & c);
-        }
-        uint32_t *sr = s + op * m;
-#pragma unroll
-        for (int j = 0; j < NCH; ++j) {
-            const size_t li = wbase + ((size_t)j * 32 + lane) * 4;
-            const uint32_t Pm = P[j] & 0x7fffffffu;
-            const uint32_t C = (((G[j] << 1) | c) + Pm) ^ Pm;
-            const uint32_t ci = (C >> lane) & 1u;
-            sg[j].apply(ci);
-            if (li < m) {
-                store_seg<4>(sr + li, sg[j].r);
-                if (li + 4 >= m && t == tiles_per_op - 1) cout[op] = sg[j].cout(ci);
-            }
-            c = ((G[j] >> 31) | ((P[j] >> 31) & (C >> 31))) & 1u;
-        }
+    // Tiles alternate between two register sets (the loop is unrolled by two
+    // so that neither is copied): tile k in A (k even) or B (k odd).  Tickets
+    // are read from s_ticket before take() re-issues that stage.
+    TileRegs<SUB, NCH> A, B;
+    unsigned long long tA = s_ticket[0];
+    if (tA < total) take(0, 0, A);
+    for (int k = 0; tA < total; k += 2) {
+        const unsigned long long tB = s_ticket[1];   // tile k + 1
+        if (tB < total) take(1, k + 1, B);
+        finish(0, tA, A);
+        if (tB >= total) break;
+        tA = s_ticket[0];                            // tile k + 2
+        if (tA < total) take(0, k + 2, A);
+        finish(1, tB, B);
     }
+    // the last block out resets the ticket counter and advances the epoch
     if (threadIdx.x == 0) {
         __threadfence();
         const unsigned long long prev = atomicAdd(&lb.counters[1], 1ull);
