@@ -241,10 +241,11 @@ DOT_API dot_status_t dot_mixed_ragged(dot_ctx_t ctx, const dot_desc_t *desc, siz
 /* Same results as dot_add / dot_sub / dot_mul, but a, b and the outputs are
  * HOST pointers (pinned memory gives asynchronous copies; pageable memory
  * works but is staged by the driver).  The library copies the operands into
- * ctx-owned device staging buffers chunk by chunk, computes, and copies the
- * results back, overlapping the copies of one chunk with the compute of
- * another.  Returns after enqueueing; the host outputs are valid once
- * `stream` has been synchronised (dot_ctx_check does that). */
+ * two ctx-owned device staging buffers chunk by chunk, computes, and copies
+ * the results back: copies in and copies out run on two ctx streams and the
+ * kernels on `stream`, so both copy directions stay busy at once.  Returns
+ * after enqueueing; the host outputs are valid once `stream` has been
+ * synchronised (dot_ctx_check does that). */
 DOT_API dot_status_t dot_add_host(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b,
                                   uint32_t *s, uint32_t *carry_out, size_t m, size_t batch,
                                   dot_stream_t stream);

@@ -79,7 +79,7 @@ DOT_API dot_status_t dot_ctx_create(dot_ctx_t *out, int device)
     }
     for (int i = 0; st == DOT_OK && i < 2; ++i)
         if (cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking) != cudaSuccess) st = DOT_ECUDA;
-    for (int i = 0; st == DOT_OK && i < 6; ++i)
+    for (int i = 0; st == DOT_OK && i < 8; ++i)
         if (cudaEventCreateWithFlags(&c->ev[i], cudaEventDisableTiming) != cudaSuccess) st = DOT_ECUDA;
     if (st != DOT_OK) {
         dot_ctx_destroy(c);
@@ -95,7 +95,7 @@ DOT_API void dot_ctx_destroy(dot_ctx_t c)
     set_device(c->device);
     cudaDeviceSynchronize();
     dot_mixed_release(c);
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < 8; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     for (int i = 0; i < 2; ++i)
         if (c->side[i]) cudaStreamDestroy(c->side[i]);

@@ -35,8 +35,10 @@ struct dot_ctx {
     // staging for the host-buffer entry points
     void *d_stage;
     size_t stage_bytes;
-    cudaStream_t side[2];
-    cudaEvent_t ev[6];   // [0,1] kernel done per side stream, [2] start, [3,4] side ends
+    cudaStream_t side[2];   // [0] copies in, [1] copies out
+    // per staging buffer: [0,1] inputs copied in, [2,3] kernel done, [4,5]
+    // results copied out; [6] call start, [7] copies out finished
+    cudaEvent_t ev[8];
     // mixed-batch scratch and captured graph (dot_mixed.cu), created on first use
     void *mixed;
     // tuned shape per (op, bit length of m); 0 = built-in choice (dot_tune.cu)
