@@ -507,17 +507,17 @@ static cudaError_t launch_warp(dot_ctx_t ctx, const dot_plan_t &pl, const uint32
 {
     const int lpo = pl.lanes_per_op, nch = pl.chunks;
     const int opw = 32 / lpo;
-    const int U = (nch == 1) ? 2 : 1;
+    const int U = (nch == 1) ? 4 : 1;
     const size_t warp_iters = dot_ceil_div(batch, (size_t)opw * U);
     const size_t blocks_needed = dot_ceil_div(warp_iters, WARP_KERNEL_THREADS / 32);
     const void *fn;
-    if (nch == 1) fn = (const void *)addsub_warp_kernel<SUB, SEG, 1, 2>;
+    if (nch == 1) fn = (const void *)addsub_warp_kernel<SUB, SEG, 1, 4>;
     else if (nch == 2) fn = (const void *)addsub_warp_kernel<SUB, SEG, 2, 1>;
     else fn = (const void *)addsub_warp_kernel<SUB, SEG, 4, 1>;
     const size_t cap = (size_t)ctx->num_sms * dot_blocks_per_sm(fn, WARP_KERNEL_THREADS, 0);
     const unsigned grid = (unsigned)(blocks_needed < cap ? blocks_needed : cap);
     if (nch == 1)
-        addsub_warp_kernel<SUB, SEG, 1, 2><<<grid, WARP_KERNEL_THREADS, 0, st>>>(a, b, s, cout, m, batch, lpo, nch);
+        addsub_warp_kernel<SUB, SEG, 1, 4><<<grid, WARP_KERNEL_THREADS, 0, st>>>(a, b, s, cout, m, batch, lpo, nch);
     else if (nch == 2)
         addsub_warp_kernel<SUB, SEG, 2, 1><<<grid, WARP_KERNEL_THREADS, 0, st>>>(a, b, s, cout, m, batch, lpo, nch);
     else
@@ -748,15 +748,15 @@ static dot_status_t noalloc_launch(int sms, unsigned long long *scratch, const d
 {
     if (pl.kernel == DOT_K_ADDSUB_WARP) {
         const int lpo = pl.lanes_per_op, nch = pl.chunks, opw = 32 / lpo;
-        const int U = (nch == 1) ? 2 : 1;
+        const int U = (nch == 1) ? 4 : 1;
         const size_t need = dot_ceil_div(dot_ceil_div(batch, (size_t)opw * U), WARP_KERNEL_THREADS / 32);
-        const void *fn = nch == 1 ? (const void *)addsub_warp_kernel<SUB, SEG, 1, 2>
+        const void *fn = nch == 1 ? (const void *)addsub_warp_kernel<SUB, SEG, 1, 4>
                        : nch == 2 ? (const void *)addsub_warp_kernel<SUB, SEG, 2, 1>
                                   : (const void *)addsub_warp_kernel<SUB, SEG, 4, 1>;
         const size_t cap = (size_t)sms * dot_blocks_per_sm(fn, WARP_KERNEL_THREADS, 0);
         const unsigned grid = (unsigned)(need < cap ? need : cap);
         if (nch == 1)
-            addsub_warp_kernel<SUB, SEG, 1, 2><<<grid, WARP_KERNEL_THREADS, 0, st>>>(a, b, s, cout, m, batch, lpo, nch);
+            addsub_warp_kernel<SUB, SEG, 1, 4><<<grid, WARP_KERNEL_THREADS, 0, st>>>(a, b, s, cout, m, batch, lpo, nch);
         else if (nch == 2)
             addsub_warp_kernel<SUB, SEG, 2, 1><<<grid, WARP_KERNEL_THREADS, 0, st>>>(a, b, s, cout, m, batch, lpo, nch);
         else
