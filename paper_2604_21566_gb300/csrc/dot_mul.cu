@@ -220,10 +220,13 @@ DOT_API dot_status_t dot_mul_ragged(dot_ctx_t ctx, const uint32_t *a, const uint
     if (batch == 0) return DOT_OK;
     if (!a || !b || !p || !off || !poff) return DOT_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    // size classes: R = 8 handles m <= 256, R = 16 handles 256 < m <= 512
+    // size classes: R = 8 handles m <= 256, R = 12 256 < m <= 384 and R = 16
+    // 384 < m <= 512, so that an op's ceil(m / R) lanes fill most of its warp
     rc = launch_mul_ragged<8>(ctx, a, b, p, off, poff, batch, 0, 256, st);
     if (rc != DOT_OK) return rc;
-    return launch_mul_ragged<16>(ctx, a, b, p, off, poff, batch, 257, DOT_MUL_MAX_LIMBS, st);
+    rc = launch_mul_ragged<12>(ctx, a, b, p, off, poff, batch, 257, 384, st);
+    if (rc != DOT_OK) return rc;
+    return launch_mul_ragged<16>(ctx, a, b, p, off, poff, batch, 385, DOT_MUL_MAX_LIMBS, st);
 }
 
 }  // extern "C"

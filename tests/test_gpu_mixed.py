@@ -71,7 +71,7 @@ def test_small_batches_every_bucket(D, seed):
     """Every size class incl. the boundaries between buckets, several calls
     of different lengths on one context (graph parameters updated per call)."""
     g = W.rng(300 + seed)
-    sizes = [1, 2, 3, 4, 15, 16, 17, 63, 64, 65, 127, 128, 129, 255, 256, 257, 511, 512,
+    sizes = [1, 2, 3, 4, 15, 16, 17, 63, 64, 65, 127, 128, 129, 255, 256, 257, 383, 384, 385, 511, 512,
              700, 1000, 5]
     n = 3 * len(sizes)
     op = np.array([k % 3 for k in range(n)], dtype=np.uint32)

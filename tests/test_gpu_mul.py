@@ -102,7 +102,7 @@ def test_errors(D):
 def test_ragged(D):
     import torch
     g = W.rng(41)
-    sizes = [1, 2, 3, 4, 5, 8, 16, 17, 31, 32, 33, 64, 100, 129, 256, 257, 300, 512, 7, 0]
+    sizes = [1, 2, 3, 4, 5, 8, 16, 17, 31, 32, 33, 64, 100, 129, 256, 257, 300, 383, 384, 385, 511, 512, 7, 0]
     a, b, off = W.ragged_uniform(g, sizes)
     want, poff = oracle.mul_ragged(a, b, off)
     out = torch.zeros(int(poff[-1]), dtype=torch.int32, device="cuda")
