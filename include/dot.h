@@ -260,8 +260,8 @@ DOT_API dot_status_t dot_mul_host(dot_ctx_t ctx, const uint32_t *a, const uint32
 /* Tile and limbs-per-thread shapes, chosen per context and per size class
  * (op, bit length of m).  The paper fixes its SIMD width at compile time;
  * this table and the autotuner are this library's own.  A knob value is:
- *   DOT_OP_MUL: R, the output columns each thread accumulates (4, 8 or 16;
- *               needs m <= 32 R);
+ *   DOT_OP_MUL: R, the output columns each thread accumulates (4, 8, 12 or
+ *               16; needs m <= 32 R);
  *   DOT_OP_ADD / DOT_OP_SUB: segments per thread of the tiled look-back
  *               kernel (1, 2 or 4, i.e. 1024- to 4096-limb tiles; used only
  *               for operands longer than 512 limbs).

@@ -177,6 +177,7 @@ DOT_API dot_status_t dot_mul(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b
     switch (pl.seg_limbs) {
     case 4: return launch_mul_batched<4>(ctx, pl, a, b, p, m, batch, st);
     case 8: return launch_mul_batched<8>(ctx, pl, a, b, p, m, batch, st);
+    case 12: return launch_mul_batched<12>(ctx, pl, a, b, p, m, batch, st);
     default: return launch_mul_batched<16>(ctx, pl, a, b, p, m, batch, st);
     }
 }
@@ -206,6 +207,8 @@ DOT_API dot_status_t dot_sqr(dot_ctx_t ctx, const uint32_t *a, uint32_t *p, size
                        : launch_mul_batched<4, false>(ctx, pl, a, a, p, m, batch, st);
     case 8: return sym ? launch_mul_batched<8, true>(ctx, pl, a, a, p, m, batch, st)
                        : launch_mul_batched<8, false>(ctx, pl, a, a, p, m, batch, st);
+    case 12: return sym ? launch_mul_batched<12, true>(ctx, pl, a, a, p, m, batch, st)
+                        : launch_mul_batched<12, false>(ctx, pl, a, a, p, m, batch, st);
     default: return sym ? launch_mul_batched<16, true>(ctx, pl, a, a, p, m, batch, st)
                         : launch_mul_batched<16, false>(ctx, pl, a, a, p, m, batch, st);
     }

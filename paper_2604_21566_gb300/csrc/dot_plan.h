@@ -23,7 +23,7 @@ static inline size_t dot_ceil_div(size_t a, size_t b) { return (a + b - 1) / b; 
 // Columns per thread block of the multiply for operand length m.
 static inline int dot_mul_cols(size_t m)
 {
-    return m <= 16 ? 4 : (m <= 256 ? 8 : 16);
+    return m <= 16 ? 4 : (m <= 256 ? 8 : (m <= 384 ? 12 : 16));
 }
 
 // Size bucket of the tuning table: the bit length of m (m in [2^(b-1), 2^b)).
@@ -39,11 +39,11 @@ static inline int dot_tune_bucket(size_t m)
 }
 
 // Whether `knob` is a shape the kernels implement for (op, m):
-//   mul    -- R, the columns per block: 4, 8 or 16 with m <= 32 R;
+//   mul    -- R, the columns per block: 4, 8, 12 or 16 with m <= 32 R;
 //   add/sub -- segments per thread of the tiled look-back kernel: 1, 2 or 4.
 static inline bool dot_knob_valid(int op, size_t m, int knob)
 {
-    if (op == DOT_OP_MUL) return (knob == 4 || knob == 8 || knob == 16) && m <= (size_t)32 * knob;
+    if (op == DOT_OP_MUL) return (knob == 4 || knob == 8 || knob == 12 || knob == 16) && m <= (size_t)32 * knob;
     return knob == 1 || knob == 2 || knob == 4;
 }
 

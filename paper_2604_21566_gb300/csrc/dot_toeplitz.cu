@@ -923,6 +923,7 @@ DOT_API dot_status_t dot_mul_shared(dot_ctx_t ctx, const uint32_t *fixed, const 
     switch (pl.seg_limbs) {
     case 4: return launch_shared_int<4>(ctx, pl, fixed, b, p, m, batch, st);
     case 8: return launch_shared_int<8>(ctx, pl, fixed, b, p, m, batch, st);
+    case 12: return launch_shared_int<12>(ctx, pl, fixed, b, p, m, batch, st);
     default: return launch_shared_int<16>(ctx, pl, fixed, b, p, m, batch, st);
     }
 }

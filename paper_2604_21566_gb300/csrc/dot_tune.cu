@@ -1,7 +1,7 @@
 // dot_tune.cu -- per-context tuning table and the autotuner.
 //
 // The tuned shapes are the ones the kernels take as template parameters:
-// the columns per block R of the multiply (4, 8, 16) and the segments per
+// the columns per block R of the multiply (4, 8, 12, 16) and the segments per
 // thread of the tiled look-back add/sub (1, 2, 4, i.e. 1024 to 4096-limb
 // tiles).  A context keeps one choice per (op, bit length of m); the
 // autotuner times every valid candidate on synthetic operands of the asked
@@ -26,7 +26,7 @@ static int candidates(int op, size_t m, size_t batch, int *out)
 {
     int n = 0;
     if (op == DOT_OP_MUL) {
-        const int rs[3] = {4, 8, 16};
+        const int rs[4] = {4, 8, 12, 16};
         for (int r : rs)
             if (dot_knob_valid(op, m, r)) out[n++] = r;
         return n;
