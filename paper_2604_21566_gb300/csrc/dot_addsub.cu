@@ -286,8 +286,7 @@ struct TileRegs {
 template <bool SUB, int NCH>
 __device__ __forceinline__ void tile_bulk_aggregate(const uint32_t *stage, unsigned long long ticket,
                                                     unsigned long long tiles_per_op, size_t m, int st,
-                                                    TileRegs<SUB, NCH> &tr, uint32_t (&s_wagg)[2][DOT_TILE_THREADS / 32],
-                                                    int lane, int warp)
+                                                    TileRegs<SUB, NCH> &tr, uint32_t *wagg, int lane, int warp)
 {
     constexpr unsigned long long TILE = (unsigned long long)DOT_TILE_THREADS * 4 * NCH;
     constexpr int WARP_LIMBS = 32 * 4 * NCH;
@@ -314,7 +313,7 @@ __device__ __forceinline__ void tile_bulk_aggregate(const uint32_t *stage, unsig
         tr.P[j] = wc.P;
         gp_compose(wg, wp, wc.carry_out(31), (uint32_t)(wc.P == DOT_FULL));
     }
-    if (lane == 0) s_wagg[st][warp] = wg | (wp << 1);
+    if (lane == 0) wagg[warp] = wg | (wp << 1);
 }
 
 template <bool SUB, int NCH>
@@ -353,8 +352,11 @@ addsub_tile_bulk_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint3
     extern __shared__ __align__(128) uint32_t stage[];   // [2][2][TILE]: stage, operand
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ unsigned long long s_ticket[2];
-    __shared__ uint32_t s_wagg[2][WARPS];
-    __shared__ uint32_t s_cin;
+    // per-warp aggregates of tile k in slot k % 4 and its carry-in in s_cin[k % 2]:
+    // with two CTA barriers per tile, a slot is rewritten only after every warp
+    // has passed a barrier that follows its last read
+    __shared__ uint32_t s_wagg[4][WARPS];
+    __shared__ uint32_t s_cin[2];
     const int lane = (int)lane_id();
     const int warp = (int)(threadIdx.x >> 5);
     const unsigned long long epoch = lb.counters[2];
@@ -373,32 +375,32 @@ addsub_tile_bulk_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint3
             bulk_g2s(stage + (2 * st + 1) * TILE, b + op * m + first, bytes, &s_bar[st]);
         }
     };
-    // warp 0: compose the block aggregate of the tile in stage st and publish
-    // it (INCLUSIVE when it decides the carry-out, PROPAGATE otherwise)
-    auto publish = [&](int st, unsigned long long ticket) {
+    // warp 0: compose the block aggregate of tile k and publish it (INCLUSIVE
+    // when it decides the carry-out, PROPAGATE otherwise)
+    auto publish = [&](int k, unsigned long long ticket) {
         uint32_t tg = 0, tp = 1;
 #pragma unroll
-        for (int w = 0; w < WARPS; ++w) gp_compose(tg, tp, s_wagg[st][w] & 1u, s_wagg[st][w] >> 1);
+        for (int w = 0; w < WARPS; ++w) gp_compose(tg, tp, s_wagg[k & 3][w] & 1u, s_wagg[k & 3][w] >> 1);
         const unsigned long long op = ticket / tiles_per_op, t = ticket - op * tiles_per_op;
         const bool skip = lb.skip_tile >= 0 && op == 0 && (long long)t == lb.skip_tile;
         if (lane == 0 && !skip)
             st_state(lb.state + ticket, (epoch << 2) | ((tp && t > 0) ? LB_PROP : (tg ? LB_INCL1 : LB_INCL0)));
     };
-    // all threads: wait for the tile of stage st, form its aggregates, publish,
-    // and reuse the stage for the tile two ahead
-    auto take = [&](int st, int k, TileRegs<SUB, NCH> &tr) {
+    // all threads: wait for tile k (stage st, ticket read by every thread
+    // before the call), form its aggregates, publish, and reuse the stage for
+    // tile k + 2
+    auto take = [&](int st, int k, unsigned long long ticket, TileRegs<SUB, NCH> &tr) {
         if (!mbar_wait_bounded(&s_bar[st], (uint32_t)((k >> 1) & 1), lb.wait_limit_ns) && lane == 0)
             record_status(lb.status, DOT_ETIMEOUT);
-        tile_bulk_aggregate<SUB, NCH>(stage, s_ticket[st], tiles_per_op, m, st, tr, s_wagg, lane, warp);
-        __syncthreads();   // stage st fully read; warp aggregates visible
-        const unsigned long long ticket = s_ticket[st];
-        if (warp == 0) publish(st, ticket);
-        __syncthreads();   // every thread has read s_ticket[st] before it is rewritten
+        tile_bulk_aggregate<SUB, NCH>(stage, ticket, tiles_per_op, m, st, tr, s_wagg[k & 3], lane, warp);
+        __syncthreads();   // stage st fully read, s_ticket[st] read by all; aggregates visible
+        if (warp == 0) publish(k, ticket);
         if (threadIdx.x == 0) issue(st, k + 2);
     };
-    // warp 0: carry into the tile of stage st (the look-back; a PROPAGATE tile
-    // then publishes INCLUSIVE); all threads: add it in and store the tile
-    auto finish = [&](int st, unsigned long long ticket, TileRegs<SUB, NCH> &tr) {
+    // warp 0: carry into tile k (the look-back; a PROPAGATE tile then
+    // publishes INCLUSIVE); all threads: add it in and store the tile
+    auto finish = [&](int k, unsigned long long ticket, TileRegs<SUB, NCH> &tr) {
+        const uint32_t *wagg = s_wagg[k & 3];
         if (warp == 0) {
             const unsigned long long op = ticket / tiles_per_op, t = ticket - op * tiles_per_op;
             uint32_t cin_tile = 0;
@@ -406,22 +408,21 @@ addsub_tile_bulk_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint3
                 const unsigned long long *st_op = lb.state + (ticket - t);
                 uint32_t tg = 0, tp = 1;
 #pragma unroll
-                for (int w = 0; w < WARPS; ++w) gp_compose(tg, tp, s_wagg[st][w] & 1u, s_wagg[st][w] >> 1);
+                for (int w = 0; w < WARPS; ++w) gp_compose(tg, tp, wagg[w] & 1u, wagg[w] >> 1);
                 cin_tile = lookback_carry(lb, st_op, (long long)t, epoch, lane);
                 const bool skip = lb.skip_tile >= 0 && op == 0 && (long long)t == lb.skip_tile;
                 if (tp && lane == 0 && !skip)
                     st_state(lb.state + ticket, (epoch << 2) | (cin_tile ? LB_INCL1 : LB_INCL0));
             }
-            if (lane == 0) s_cin = cin_tile;
+            if (lane == 0) s_cin[k & 1] = cin_tile;
         }
         __syncthreads();
-        uint32_t c = s_cin;
+        uint32_t c = s_cin[k & 1];
         for (int w = 0; w < warp; ++w) {
-            const uint32_t g = s_wagg[st][w] & 1u, p = s_wagg[st][w] >> 1;
+            const uint32_t g = wagg[w] & 1u, p = wagg[w] >> 1;
             c = g | (p & c);
         }
         tile_bulk_apply<SUB, NCH>(tr, s, cout, ticket, tiles_per_op, m, c, lane, warp);
-        __syncthreads();   // s_cin and s_wagg[st] are read before they are rewritten
     };
 
     if (threadIdx.x == 0) {
@@ -438,15 +439,15 @@ addsub_tile_bulk_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint3
     // are read from s_ticket before take() re-issues that stage.
     TileRegs<SUB, NCH> A, B;
     unsigned long long tA = s_ticket[0];
-    if (tA < total) take(0, 0, A);
+    if (tA < total) take(0, 0, tA, A);
     for (int k = 0; tA < total; k += 2) {
         const unsigned long long tB = s_ticket[1];   // tile k + 1
-        if (tB < total) take(1, k + 1, B);
-        finish(0, tA, A);
+        if (tB < total) take(1, k + 1, tB, B);
+        finish(k, tA, A);
         if (tB >= total) break;
         tA = s_ticket[0];                            // tile k + 2
-        if (tA < total) take(0, k + 2, A);
-        finish(1, tB, B);
+        if (tA < total) take(0, k + 2, tA, A);
+        finish(k + 1, tB, B);
     }
     // the last block out resets the ticket counter and advances the epoch
     if (threadIdx.x == 0) {
