@@ -178,12 +178,13 @@ DOT_API dot_status_t dot_sqr(dot_ctx_t ctx, const uint32_t *a, uint32_t *p, size
                              dot_stream_t stream);
 
 /* Batched product of any size, p[k] = a[k] * b[k] as 2m limbs: the
- * appendix's MPN-KARATSUBA (Karatsuba, or Toom-Cook 2-way), whose recursion
- * bottoms out at the base case (Sec. 2): above DOT_MUL_MAX_LIMBS limbs each
- * level splits at h = ceil(m / 2), forms |A_H - A_L| and |B_H - B_L| with
- * their signs, runs the three half-size products as one batched product
- * over 3 x batch operations, and combines P1 b^2 + (P1 + P0 - P2) b + P0 on
- * the add path; at or below DOT_MUL_MAX_LIMBS it is dot_mul.  Layout as
+ * appendix's MPN-KARATSUBA (Karatsuba, or Toom-Cook 2-way), a recursion that
+ * ends in the column-sum base case (Sec. 2): above 384 limbs each level
+ * splits at h = ceil(m / 2), forms |A_H - A_L| and |B_H - B_L| with their
+ * signs, runs the three half-size products as one batched product over
+ * 3 x batch operations, and combines P1 b^2 + (P1 + P0 - P2) b + P0 on the
+ * add path; at or below 384 limbs it is dot_mul (whose 385..512-limb shape
+ * is slower than one more level over 193..256-limb products).  Layout as
  * dot_mul; 1 <= m <= DOT_KARA_MAX_LIMBS (else DOT_EINVAL), m == 0 no-op.
  * Uses a workspace owned by ctx (about 14 m batch bytes per level, grown on
  * demand with a device synchronisation; DOT_ENOMEM if it cannot grow):

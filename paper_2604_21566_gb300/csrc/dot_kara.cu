@@ -1,8 +1,8 @@
 // dot_kara.cu -- batched Karatsuba multiplication above the base-case size.
 //
-// The appendix's MPN-KARATSUBA (Karatsuba, or Toom-Cook 2-way; the recursion
-// of Sec. 2 that "eventually bottoms out at this same base-case routine"):
-// with A = A_H b + A_L, B = B_H b + B_L, b = X^h,
+// The appendix's MPN-KARATSUBA (Karatsuba, or Toom-Cook 2-way; Sec. 2 notes
+// that such recursions end in the same schoolbook base case that the column
+// sums implement): with A = A_H b + A_L, B = B_H b + B_L, b = X^h,
 //     P1 = A_H B_H,  P0 = A_L B_L,  P_D = |A_H - A_L| |B_H - B_L|,
 //     P2 = sign(A_H - A_L) sign(B_H - B_L) P_D,
 //     A B = P1 b^2 + (P1 + P0 - P2) b + P0.
@@ -13,13 +13,19 @@
 //     almost always ends at the first), then one subtraction in the right
 //     order with the warp lookahead;
 //   * the three half-size products run as ONE batched product over 3x the
-//     ops (the column-sum multiply at h <= DOT_MUL_MAX_LIMBS, else the next
+//     ops (the column-sum multiply at h <= KARA_BASE_LIMBS, else the next
 //     level of this recursion);
 //   * kara_combine_kernel (one warp per op) forms Q = P1 + P0 -/+ P_D
 //     (2h limbs and a top word), then P = (P0 || P1) + Q b with the same
 //     lookahead -- the additions and subtractions the paper notes multiply
 //     with the recursion depth run on the add path.
 // Odd m splits at h = ceil(m / 2); A_H and B_H are zero-padded to h limbs.
+//
+// Base case: up to 384 limbs, although dot_mul takes 512.  Between 385 and
+// 512 limbs the column-sum multiply needs 16 columns per lane, the slowest of
+// its shapes (5.4e12 limb products/s against 6.0e12-6.5e12 with 8 or 12), and
+// one more level replaces each such product by three of at most 256 limbs
+// (3/4 of the products) for some memory-bound split and combine work.
 #include <string.h>
 
 #include "dot_internal.cuh"
@@ -27,6 +33,7 @@
 #include "dot_warp_op.cuh"
 
 #define KARA_THREADS 256   // 8 warps, one op each
+#define KARA_BASE_LIMBS 384
 
 // The sign-and-magnitude difference |x - y| of two h-limb rows (x, y read
 // through lx, ly), written through st; returns 1 when x < y.
@@ -132,7 +139,7 @@ kara_combine_kernel(const uint32_t *z, const uint32_t *neg, uint32_t *q, uint32_
 // half-size products, 2 batch h for Q, batch for the signs.
 static size_t kara_work_words(size_t m, size_t batch)
 {
-    if (m <= DOT_MUL_MAX_LIMBS) return 0;
+    if (m <= KARA_BASE_LIMBS) return 0;
     const size_t h = (m + 1) / 2;
     return 14 * batch * h + batch + 4 + kara_work_words(h, 3 * batch);
 }
@@ -147,7 +154,7 @@ static unsigned kara_grid(dot_ctx_t ctx, const void *fn, size_t batch)
 static dot_status_t kara(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b, uint32_t *p, size_t m, size_t batch,
                          uint32_t *work, cudaStream_t st)
 {
-    if (m <= DOT_MUL_MAX_LIMBS) return dot_mul(ctx, a, b, p, m, batch, (dot_stream_t)st);
+    if (m <= KARA_BASE_LIMBS) return dot_mul(ctx, a, b, p, m, batch, (dot_stream_t)st);
     const size_t h = (m + 1) / 2;
     uint32_t *wa = work, *wb = wa + 3 * batch * h, *z = wb + 3 * batch * h, *q = z + 6 * batch * h;
     uint32_t *neg = q + 2 * batch * h;
@@ -176,7 +183,7 @@ DOT_API dot_status_t dot_mul_karatsuba(dot_ctx_t ctx, const uint32_t *a, const u
     const size_t in = m * batch * 4, out = 2 * in;
     if (any_overlap(p, out, a, in) || any_overlap(p, out, b, in)) return DOT_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    if (m <= DOT_MUL_MAX_LIMBS) return dot_mul(ctx, a, b, p, m, batch, stream);
+    if (m <= KARA_BASE_LIMBS) return dot_mul(ctx, a, b, p, m, batch, stream);
     uint32_t *work = nullptr;
     rc = dot_work(ctx, kara_work_words(m, batch) * 4, (void **)&work);
     if (rc != DOT_OK) return rc;

@@ -27,7 +27,7 @@ def run(D, x, y):
     return host(p)
 
 
-@pytest.mark.parametrize("m", [1, 100, 512, 513, 514, 600, 1023, 1024, 1025, 2048, 3001, 4096])
+@pytest.mark.parametrize("m", [1, 100, 384, 385, 512, 513, 514, 600, 1023, 1024, 1025, 2048, 3001, 4096])
 def test_sizes(D, m):
     g = W.rng(4000 + m)
     batch = 9 if m <= 1025 else 4
@@ -52,7 +52,7 @@ def test_value_classes(D, cls):
 
 
 def test_several_levels(D):
-    """16384 limbs: five halvings down to 512-limb base cases (3^5 = 243
+    """16384 limbs: six halvings down to 256-limb base cases (3^6 = 729
     base products per operation)."""
     g = W.rng(4200)
     x, y = W.class_operands(g, "uniform", 2, 16384)
