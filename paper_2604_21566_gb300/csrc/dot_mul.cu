@@ -34,7 +34,7 @@
 // Batched product: runs of T = m'/R lanes, 32/T ops per warp.  SQR: the
 // square of a (b is a), with half the partial products.
 template <int R, bool SQR>
-__global__ void __launch_bounds__(MUL_WARPS * 32, dot_mul_min_blocks(R))
+__global__ void __launch_bounds__(MUL_WARPS * 32, dot_mul_min_blocks(R, SQR))
 mul_batched_kernel(const uint32_t *a, const uint32_t *b, uint32_t *p, int m, int mp, int T,
                    size_t batch, int vec_in, int vec_out)
 {

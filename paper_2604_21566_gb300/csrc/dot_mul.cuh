@@ -8,8 +8,14 @@
 // Resident blocks per SM the compiler must allow (caps registers per thread).
 // Both blocks' sums stay live through the row loop (colsum_pair): R = 8 fits
 // 4 blocks of 4 warps (128 registers), R = 4 fits 6 (80 registers; the
-// smallest products need the occupancy more), R = 16 needs ~170-190.
-__host__ __device__ constexpr int dot_mul_min_blocks(int R) { return R <= 4 ? 6 : (R <= 8 ? 4 : 1); }
+// smallest products need the occupancy more), and R = 16 and the R = 12
+// square fit 3 (168 registers, without spills; left free the compiler takes
+// up to ~200 and only 2 blocks fit).  The R = 12 general product already
+// fits 3 when left free and measured 7% slower with the cap.
+__host__ __device__ constexpr int dot_mul_min_blocks(int R, bool sqr = false)
+{
+    return R <= 4 ? 6 : (R <= 8 ? 4 : (R == 12 && !sqr ? 1 : 3));
+}
 
 // Column sums of one block of R columns, kept as three 32-bit words each:
 // S_k = s2[k] X^2 + s1[k] X + s0[k]  (S_k < m 2^64 needs 64 + log2 m bits).
