@@ -194,7 +194,8 @@ DOT_API dot_status_t dot_sqr(dot_ctx_t ctx, const uint32_t *a, uint32_t *p, size
     const size_t in = m * batch * 4, out = 2 * in;
     if (any_overlap(p, out, a, in)) return DOT_EINVAL;
     dot_plan_t pl;
-    rc = dot_make_plan(DOT_OP_MUL, m, batch, true, &pl, ctx->tune[DOT_OP_MUL][dot_tune_bucket(m)]);
+    const int knob = ctx->tune[DOT_OP_MUL][dot_tune_bucket(m)];
+    rc = dot_make_plan(DOT_OP_MUL, m, batch, true, &pl, knob ? knob : dot_mul_cols(m, true));
     if (rc != DOT_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     // Below 128 limbs the rows near the diagonal, summed one column at a time,

@@ -21,9 +21,29 @@ enum {
 static inline size_t dot_ceil_div(size_t a, size_t b) { return (a + b - 1) / b; }
 
 // Columns per thread block of the multiply for operand length m.
-static inline int dot_mul_cols(size_t m)
+static inline int dot_mul_cols(size_t m, bool sqr = false)
 {
-    return m <= 16 ? 4 : (m <= 256 ? 8 : (m <= 384 ? 12 : 16));
+    // Above 16 limbs: the R in {8, 12, 16} that leaves the fewest lane-steps
+    // idle.  A warp holds floor(32 / T) ops of T = ceil(m / R) lanes; each lane
+    // sums m' + R rows of R columns (m' = T R) for m^2 useful products per op.
+    // (R = 4 scores as well at 32-64 limbs but measured slower: it reuses
+    // each window value for only 4 products.)  A square sums its up to 1.5 R
+    // near-diagonal rows per block one column at a time, which costs R = 16
+    // too much: it takes 16 only above 384 limbs, where nothing else fits.
+    if (m <= 16) return 4;
+    int best = 8;
+    double best_eff = -1.0;
+    const int rs[3] = {8, 12, 16};
+    for (int R : rs) {
+        if (m > (size_t)32 * R || (sqr && R == 16 && m <= 384)) continue;
+        const size_t T = (m + R - 1) / R, mp = T * R;
+        const double eff = (double)(32 / T) * (double)m * (double)m / (32.0 * (double)(mp + R) * R);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = R;
+        }
+    }
+    return best;
 }
 
 // Size bucket of the tuning table: the bit length of m (m in [2^(b-1), 2^b)).
