@@ -124,7 +124,9 @@ def test_ragged(D):
 def test_host_buffers(D):
     import torch
     g = W.rng(43)
-    for m, batch in ((32, 50000), (256, 3000), (13, 777)):
+    # (64, 150000): five 32 MB staging chunks, the last one partial, so both
+    # staging buffers are reused
+    for m, batch in ((32, 50000), (256, 3000), (13, 777), (64, 150000)):
         x, y = W.class_operands(g, "uniform", batch, m)
         xs = torch.from_numpy(x.view(np.int32)).pin_memory()
         ys = torch.from_numpy(y.view(np.int32)).pin_memory()
