@@ -545,9 +545,12 @@ static dot_status_t launch_tile(dot_ctx_t ctx, const dot_plan_t &pl, const uint3
                                         : (const void *)addsub_tile_bulk_kernel<SUB, 4>;
         if (cudaFuncSetAttribute(fb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return DOT_ECUDA;
-        // every block resident at once (the static schedule's look-back relies on it)
+        // every block resident at once (the static schedule's look-back relies
+        // on it), and as few blocks as give every block the same number of
+        // tiles: a last round that only part of the blocks work on ends later
         const size_t cap = (size_t)ctx->num_sms * dot_blocks_per_sm(fb, DOT_TILE_THREADS, smem);
-        const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
+        const size_t rounds = dot_ceil_div(tiles, cap);
+        const unsigned grid = (unsigned)dot_ceil_div(tiles, rounds);
         void *args[] = {(void *)&a, (void *)&b, (void *)&s, (void *)&cout, (void *)&m, (void *)&batch,
                         (void *)&tpo, (void *)&lb};
         const cudaError_t e = cudaLaunchCooperativeKernel(fb, dim3(grid), dim3(DOT_TILE_THREADS), args, smem, st);
