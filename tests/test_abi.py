@@ -55,10 +55,28 @@ def test_plans():
     p = dot.plan(dot.OP_ADD, 513, 3)
     assert p.kernel == 2 and p.tiles == 1
     # multiply: two column blocks per lane, R columns each
-    for m, R, T in ((8, 4, 2), (32, 8, 4), (128, 8, 16), (256, 8, 32), (512, 16, 32), (100, 8, 13)):
+    for m, R, T in ((8, 4, 2), (32, 8, 4), (128, 8, 16), (256, 8, 32), (512, 16, 32), (100, 8, 13),
+                    (96, 12, 8), (150, 16, 10), (192, 12, 16), (300, 12, 25), (384, 12, 32), (385, 16, 25)):
         p = dot.plan(dot.OP_MUL, m, 1)
         assert (p.kernel, p.seg_limbs, p.lanes_per_op) == (3, R, T), m
         assert p.m_pad == R * T
+
+
+def test_mul_columns_fill_the_warp():
+    """Above 16 limbs the default columns per lane R is the one of 8, 12, 16
+    that leaves the fewest lane-steps idle: a warp holds floor(32 / T) ops of
+    T = ceil(m / R) lanes, each lane summing m' + R rows of R columns."""
+    from fractions import Fraction
+
+    def useful(m, R):
+        T = -(-m // R)
+        return Fraction((32 // T) * m * m, 32 * (T * R + R) * R)
+
+    for m in range(17, 513):
+        cands = [R for R in (8, 12, 16) if m <= 32 * R]
+        best = max(useful(m, R) for R in cands)
+        want = min(R for R in cands if useful(m, R) == best)
+        assert dot.plan(dot.OP_MUL, m, 1).seg_limbs == want, m
     with pytest.raises(dot.DotError):
         dot.plan(dot.OP_MUL, 513, 1)
     with pytest.raises(dot.DotError):
