@@ -549,6 +549,27 @@ def suite(args):
                            "per_sm_clk": IMAD_PER_SM_CLK, "algorithmic_imad_per_product": 2},
               "sizes": rows})
 
+    if want("mulx"):
+        # -- batched multiply between and above the workload's sizes: one size
+        # for each further column shape (12 columns on 16 lanes, 12 on 25, 16)
+        rows = []
+        for m in (192, 300, 512):
+            x, y, _ = W.batched_mul(m)
+            a, b = dv(x), dv(y)
+            p = torch.empty((x.shape[0], 2 * m), dtype=torch.int32, device="cuda")
+            ms = _event_ms(lambda: dot.mul(a, b, p, ctx=ctx), 20, stream)
+            sel = np.random.default_rng(m).integers(0, x.shape[0], 256)
+            ok = np.array_equal(hs(p)[sel], oracle.mul(x[sel], y[sel], threads=oracle.cores()))
+            prods = x.shape[0] * m * m
+            imad = 2.0 * prods / (ms * 1e-3)
+            rows.append({"m_limbs": m, "bits": 32 * m, "ops": x.shape[0], "ms": round(ms, 4),
+                         "cols_per_lane": dot.plan(dot.OP_MUL, m, x.shape[0]).seg_limbs,
+                         "tera_limb_products_s": round(prods / (ms * 1e-3) / 1e12, 3),
+                         "roofline": {"bound": "alu", "achieved_imad_per_s": imad, "peak": peak,
+                                      "frac": round(imad / peak, 4)},
+                         "bit_exact_sample": bool(ok)})
+        emit({"workload": "batched multiply: 2^16 pairs at 6144/9600/16384 bits", "sizes": rows})
+
     if want("sqr"):
         # -- batched square (half the partial products) vs the general product
         rows = []
@@ -676,7 +697,7 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run only the small ncu case of the dominant kernel")
     ap.add_argument("--launches", type=int, default=3)
-    ap.add_argument("--only", default="", help="--suite rows to run: mix,mul,sqr,kara,mixed,shared")
+    ap.add_argument("--only", default="", help="--suite rows to run: mix,mul,mulx,sqr,kara,mixed,shared")
     ap.add_argument("--case", choices=["add", "long", "mul", "shared"], default="add",
                     help="which kernel --profile-case runs")
     ap.add_argument("--gpus", type=int, default=1)
