@@ -26,8 +26,11 @@ def run(D, x, y):
     return host(p)
 
 
-SIZES = list(range(1, 41)) + [47, 63, 64, 65, 96, 100, 127, 128, 129, 200, 255, 256, 257,
-                              300, 384, 500, 511, 512]
+# every column shape: 4 / 8 / 12 / 16 columns per lane, with 1 to 8 ops per
+# warp (e.g. 96: 12 columns, 4 ops; 150 and 160: 16 columns, 3 ops of 10
+# lanes; 192: 12 columns, 2 ops)
+SIZES = list(range(1, 41)) + [47, 63, 64, 65, 96, 100, 127, 128, 129, 150, 160, 192, 193, 200, 255, 256,
+                              257, 300, 384, 385, 500, 511, 512]
 
 
 @pytest.mark.parametrize("m", SIZES)

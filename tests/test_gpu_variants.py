@@ -126,8 +126,8 @@ def test_variant_errors(D):
     assert ctx.check() == D.OK
 
 
-@pytest.mark.parametrize("m", [1, 2, 3, 4, 7, 8, 9, 15, 16, 17, 31, 32, 33, 63, 64, 65, 100, 128, 255, 256, 257,
-                               511, 512])
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 7, 8, 9, 15, 16, 17, 31, 32, 33, 63, 64, 65, 96, 100, 128, 150, 160,
+                               192, 255, 256, 257, 300, 384, 385, 511, 512])
 def test_square(D, m):
     g = W.rng(3500 + m)
     x, _ = W.class_operands(g, "uniform", 67, m)
