@@ -5,7 +5,7 @@ Only the test suite, ``__graft_entry__.smoke()`` and the bench's CPU-baseline
 never loads it, and it never loads the product library: the two share no code.
 
 ``dot_oracle.c`` holds the arithmetic (Theorem 1 / Theorem 2 definitions, the
-row-wise schoolbook, and a restatement of Alg. 2); this module only compiles it
+row-wise schoolbook, and Theorem 2's column-sum form); this module only compiles it
 with gcc and marshals numpy arrays into it.  Every function is pinned by the
 ``-m "not gpu"`` tests against Python's own big integers, closed forms,
 invariants, brute force on <= 64-bit inputs and the m = 5 worked example of
@@ -49,7 +49,7 @@ def bind(path: str):
         f = getattr(L, name)
         f.argtypes = [_u32p, _u32p, _u32p, _u32p, _sz, _sz]
         f.restype = ctypes.c_int
-    for name in ("oracle_mul", "oracle_mul_vnc"):
+    for name in ("oracle_mul", "oracle_mul_columns"):
         f = getattr(L, name)
         f.argtypes = [_u32p, _u32p, _u32p, _sz, _sz]
         f.restype = ctypes.c_int
@@ -62,8 +62,8 @@ def bind(path: str):
     L.oracle_mixed.argtypes = [_u32p, _u32p, _u64p, _u64p, _u64p, _sz,
                                _u32p, _u32p, _u32p, _u32p]
     L.oracle_mixed.restype = ctypes.c_int
-    L.oracle_vnc_pairs.argtypes = [_sz, _i32p, _i32p, _i32p]
-    L.oracle_vnc_pairs.restype = ctypes.c_int
+    L.oracle_column_pairs.argtypes = [_sz, _i32p, _i32p, _i32p]
+    L.oracle_column_pairs.restype = ctypes.c_int
     for name in ("oracle_add_gen", "oracle_sub_gen"):
         f = getattr(L, name)
         f.argtypes = [_u32p, _sz, _u32p, _sz, _u32p, _u32p, _u32p, _sz]
@@ -178,22 +178,24 @@ def sqr(a):
     return p
 
 
-def mul_vnc(a, b):
-    """Alg. 2 (vertical and crosswise, Phases 1-5) restated; 2m limbs."""
+def mul_columns(a, b):
+    """P = A * B (2m limbs) as Theorem 2's column sums S_c = sum_{i+j=c} A_i B_j
+    followed by one carry pass."""
     a, b = _batched(a, b)
     B, m = a.shape
     p = np.empty((B, 2 * m), dtype=np.uint32)
-    _check(lib().oracle_mul_vnc(_p32(a), _p32(b), _p32(p), m, B), "oracle_mul_vnc")
+    _check(lib().oracle_mul_columns(_p32(a), _p32(b), _p32(p), m, B), "oracle_mul_columns")
     return p
 
 
-def vnc_pairs(m: int):
-    """Alg. 2 Phase 1 gather order: (i list, j list, pairs per column)."""
+def column_pairs(m: int):
+    """The (i, j) pairs of every column c = i + j, column by column, i
+    ascending: (i list, j list, pairs per column)."""
     ia = np.empty(m * m, dtype=np.int32)
     jb = np.empty(m * m, dtype=np.int32)
     nc = np.empty(2 * m - 1, dtype=np.int32)
-    _check(lib().oracle_vnc_pairs(m, ia.ctypes.data_as(_i32p), jb.ctypes.data_as(_i32p),
-                                  nc.ctypes.data_as(_i32p)), "oracle_vnc_pairs")
+    _check(lib().oracle_column_pairs(m, ia.ctypes.data_as(_i32p), jb.ctypes.data_as(_i32p),
+                                     nc.ctypes.data_as(_i32p)), "oracle_column_pairs")
     return ia, jb, nc
 
 
@@ -209,11 +211,13 @@ def _run_rows(fn, a, b, out, carry, m, B, threads, out_limbs):
             args.append(_p32(carry[lo:hi]))
         return fn(*args, m, n)
 
-    if threads <= 1 or B < 2 * threads:
+    # a few long rows still spread over min(threads, B) workers
+    workers = min(threads, B)
+    if workers <= 1:
         _check(call(0, B), fn.__name__)
         return
-    step = (B + threads - 1) // threads
-    with ThreadPoolExecutor(max_workers=threads) as ex:
+    step = (B + workers - 1) // workers
+    with ThreadPoolExecutor(max_workers=workers) as ex:
         rcs = list(ex.map(lambda lo: call(lo, min(B, lo + step)), range(0, B, step)))
     for rc in rcs:
         _check(rc, fn.__name__)
@@ -257,7 +261,8 @@ def mixed(op, m, a_off, b_off, r_off, a, b, r_len_total):
     a, b = _c(a), _c(b)
     n = op.size
     r = np.zeros(int(r_len_total), dtype=np.uint32)
-    c = np.empty(n, dtype=np.uint32)
+    # a sentinel, so that a carry slot the oracle failed to write shows
+    c = np.full(n, 0xFFFFFFFF, dtype=np.uint32)
     _check(lib().oracle_mixed(_p32(op), _p32(m), _p64(a_off), _p64(b_off), _p64(r_off), n,
                               _p32(a), _p32(b), _p32(r), _p32(c)), "oracle_mixed")
     return r, c

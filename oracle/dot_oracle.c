@@ -24,14 +24,15 @@
  * The add/sub loops are the textbook S_i = A_i + B_i + C_{i-1} recurrence
  * (Sec. 2.2 and Alg. 3, MPN-ADD-M) with 64-bit intermediates; the product is
  * the ROW-wise schoolbook (operand scanning), deliberately not the column form
- * the GPU uses.  oracle_mul_vnc is a separate restatement of Alg. 2
- * (vertical-and-crosswise, Phases 1-5 in the paper's order) kept to check the
- * paper's own column algorithm; it is not the parity target.
+ * the GPU uses.  oracle_mul_columns states the product a second way, as
+ * Theorem 2's column sums followed by one carry pass, to check the column
+ * identity the paper's multiplication rests on; it is not the parity target.
  *
  * Readings where the paper is silent (listed in the design notes):
  *   - limbs are 32-bit (the paper uses 64 / 52); results are radix-free;
- *   - the product has exactly 2m limbs; Alg. 2's "prepend carry" branch is
- *     unreachable for A, B < X^m, so oracle_mul_vnc reports it as an error;
+ *   - the product has exactly 2m limbs; a carry past limb 2m-1 (Alg. 2's
+ *     "prepend" case) is unreachable for A, B < X^m, so oracle_mul_columns
+ *     reports it as an error;
  *   - subtraction with A < B wraps modulo X^m and returns borrow 1;
  *   - dot_add / dot_sub take no carry-in (Alg. 1 starts with c_out = 0);
  *     the variants take one, and any nonzero carry-in word counts as 1.
@@ -165,96 +166,72 @@ int oracle_mixed(const uint32_t *op, const uint32_t *mlimbs, const uint64_t *a_o
     return 0;
 }
 
-/* ---- Alg. 2 (DoT-Mul-Words) restated, Phases 1-5 in the paper's order ----
- * Phase 1 gathers, for each column c = 0..2m-2 and each (i, j) with i+j = c
- * (i ascending), A_i into M_a and B_j into M_b.  Phase 2 forms every partial
- * product against a zero accumulator, split into a low and a high k-bit half.
- * Phase 3 walks the columns with num_pairs = min(c+1, m, 2m-1-c), adding the
- * low halves into col[c] and the high halves into col[c+1].  Phase 4 copies
- * the column values into P, and Phase 5 is one sequential carry pass over the
- * 2m entries.  Column values are kept in 64 bits: col < 2m * 2^32.
- * The SIMD chunking (step w) of Phase 2 does not change any value and is not
- * reproduced.  Returns -2 if Phase 5 leaves a nonzero carry (the "prepend"
- * branch, unreachable for m-limb inputs). */
-static int vnc_one(const uint32_t *A, const uint32_t *B, uint32_t *P, size_t m,
-                   uint32_t *Ma, uint32_t *Mb, uint32_t *Plo, uint32_t *Phi,
-                   uint64_t *col)
+/* ---- Theorem 2's column form: A * B = sum_c S_c X^c ----------------------
+ * S_c = sum over the index pairs (i, j) with i + j = c of A_i B_j, for the
+ * 2m - 1 columns c = 0 .. 2m-2.  A column sum exceeds one limb, so it is kept
+ * as two 64-bit words: `lo` sums the low 32-bit halves of its products and
+ * `hi` their high halves, S_c = lo + hi X (each word below m 2^32).  The
+ * product's limbs then come out of one pass from the least significant end,
+ * limb c taking column c's `lo`, column c-1's `hi` and the running carry.
+ * This is the paper's identity with none of the SIMD staging (no gathered
+ * operand arrays, no stored half products); it is a second, independent
+ * statement of the product next to the row-wise schoolbook above.  A carry
+ * left over after limb 2m-1 would mean a (2m+1)-limb product, impossible for
+ * m-limb operands: it is reported as -2. */
+static int columns_one(const uint32_t *A, const uint32_t *B, uint32_t *P, size_t m,
+                       uint64_t *lo, uint64_t *hi)
 {
-    const size_t mm = m * m;
-    size_t idx_a = 0, idx_b = 0;
-    /* Phase 1 */
     for (size_t c = 0; c + 1 < 2 * m; ++c) {
-        for (size_t i = 0; i <= c; ++i) {
-            size_t j = c - i;
-            if (i >= m || j >= m) continue;
-            Ma[idx_a++] = A[i];
-            Mb[idx_b++] = B[j];
+        const size_t i_first = c >= m ? c - (m - 1) : 0;
+        const size_t i_last = c < m ? c : m - 1;
+        uint64_t l = 0, h = 0;
+        for (size_t i = i_first; i <= i_last; ++i) {
+            const uint64_t prod = (uint64_t)A[i] * (uint64_t)B[c - i];
+            l += prod & 0xFFFFFFFFu;
+            h += prod >> 32;
         }
+        lo[c] = l;
+        hi[c] = h;
     }
-    if (idx_a != mm || idx_b != mm) return -3;
-    /* Phase 2 */
-    for (size_t t = 0; t < mm; ++t) {
-        uint64_t prod = (uint64_t)Ma[t] * (uint64_t)Mb[t];
-        Plo[t] = (uint32_t)prod;
-        Phi[t] = (uint32_t)(prod >> 32);
-    }
-    /* Phase 3 */
-    for (size_t c = 0; c < 2 * m; ++c) col[c] = 0;
-    size_t idx = 0;
-    for (size_t c = 0; c + 1 < 2 * m; ++c) {
-        size_t num_pairs = c + 1;
-        if (m < num_pairs) num_pairs = m;
-        if (2 * m - 1 - c < num_pairs) num_pairs = 2 * m - 1 - c;
-        for (size_t q = 0; q < num_pairs; ++q) {
-            size_t t = idx + q;
-            col[c] += Plo[t];
-            col[c + 1] += Phi[t];
-        }
-        idx += num_pairs;
-    }
-    /* Phase 4 + Phase 5 */
     uint64_t carry = 0;
     for (size_t c = 0; c < 2 * m; ++c) {
-        uint64_t v = col[c] + carry;
-        carry = v >> 32;
-        P[c] = (uint32_t)v;
+        uint64_t t = carry;
+        if (c + 1 < 2 * m) t += lo[c];
+        if (c >= 1) t += hi[c - 1];
+        P[c] = (uint32_t)t;
+        carry = t >> 32;
     }
     return carry ? -2 : 0;
 }
 
-int oracle_mul_vnc(const uint32_t *a, const uint32_t *b, uint32_t *p, size_t m, size_t batch)
+int oracle_mul_columns(const uint32_t *a, const uint32_t *b, uint32_t *p, size_t m, size_t batch)
 {
     if (batch && m && (!a || !b || !p)) return -1;
     if (!m || !batch) return 0;
-    size_t mm = m * m;
-    uint32_t *Ma = malloc(mm * sizeof *Ma), *Mb = malloc(mm * sizeof *Mb);
-    uint32_t *Plo = malloc(mm * sizeof *Plo), *Phi = malloc(mm * sizeof *Phi);
-    uint64_t *col = malloc(2 * m * sizeof *col);
-    int rc = (Ma && Mb && Plo && Phi && col) ? 0 : -4;
+    uint64_t *lo = malloc(2 * m * sizeof *lo), *hi = malloc(2 * m * sizeof *hi);
+    int rc = (lo && hi) ? 0 : -4;
     for (size_t k = 0; k < batch && rc == 0; ++k)
-        rc = vnc_one(a + k * m, b + k * m, p + 2 * k * m, m, Ma, Mb, Plo, Phi, col);
-    free(Ma); free(Mb); free(Plo); free(Phi); free(col);
+        rc = columns_one(a + k * m, b + k * m, p + 2 * k * m, m, lo, hi);
+    free(lo);
+    free(hi);
     return rc;
 }
 
-/* The Phase 1 gather order of Alg. 2 as (i, j) index pairs, and the number of
- * pairs per column, for the structural checks of the m = 5 worked example.
- * ia, jb hold m*m entries; ncol holds 2m-1 entries. */
-int oracle_vnc_pairs(size_t m, int32_t *ia, int32_t *jb, int32_t *ncol)
+/* The index pairs of each column, column by column (c = 0 .. 2m-2) and, inside
+ * a column, by ascending i: the order in which Sec. 3.2's m = 5 walkthrough
+ * lists them.  ia, jb hold m*m entries; ncol holds the 2m-1 pair counts. */
+int oracle_column_pairs(size_t m, int32_t *ia, int32_t *jb, int32_t *ncol)
 {
     if (!m || !ia || !jb || !ncol) return -1;
     size_t t = 0;
     for (size_t c = 0; c + 1 < 2 * m; ++c) {
-        int32_t n = 0;
-        for (size_t i = 0; i <= c; ++i) {
-            size_t j = c - i;
-            if (i >= m || j >= m) continue;
+        const size_t i_first = c >= m ? c - (m - 1) : 0;
+        const size_t i_last = c < m ? c : m - 1;
+        for (size_t i = i_first; i <= i_last; ++i, ++t) {
             ia[t] = (int32_t)i;
-            jb[t] = (int32_t)j;
-            ++t;
-            ++n;
+            jb[t] = (int32_t)(c - i);
         }
-        ncol[c] = n;
+        ncol[c] = (int32_t)(i_last - i_first + 1);
     }
     return t == m * m ? 0 : -3;
 }

@@ -7,7 +7,7 @@
   (2^n - 1)^2 = 2^{2n} - 2^{n+1} + 1;
 * invariants: (a + b) - b = a, a - a = 0, a + b = b + a, ab = ba,
   a (b + c) = ab + ac, a * 1 = a, a * 0 = 0, a * X^j = shift;
-* the m = 5 worked example of Alg. 2 (Sec. 3.2), tests/golden;
+* the m = 5 worked example of Sec. 3.2, tests/golden;
 * the mpn-style variants (carry-in, zero-padded shorter operand) and the
   square, against Python's integers and closed forms;
 * the carry-probability lemma of the appendix (Pr[carry] = 1/2 - 2^-(k+1)).
@@ -55,12 +55,12 @@ def pin_python_int_mul():
                 assert to_int(p[k]) == to_int(x[k]) * to_int(y[k]), (m, cls, k)
 
 
-def pin_python_int_mul_vnc():
+def pin_python_int_mul_columns():
     g = W.rng(13)
     for m in (1, 2, 3, 4, 5, 8, 17, 64):
         for cls in ("uniform", "max_pair", "ones", "sparse"):
             x, y = W.class_operands(g, cls, 4, m)
-            p = oracle.mul_vnc(x, y)
+            p = oracle.mul_columns(x, y)
             for k in range(x.shape[0]):
                 assert to_int(p[k]) == to_int(x[k]) * to_int(y[k]), (m, cls, k)
 
@@ -109,7 +109,7 @@ def pin_closed_forms():
         if m == 1:
             want = np.array([1, 0xFFFFFFFE], dtype=np.uint32)
         assert (oracle.mul(ones, ones)[0] == want).all(), m
-        assert (oracle.mul_vnc(ones, ones)[0] == want).all(), m
+        assert (oracle.mul_columns(ones, ones)[0] == want).all(), m
 
 
 def pin_invariants():
@@ -149,17 +149,19 @@ def pin_invariants():
             assert (p[:, j:j + m] == a).all() and not p[:, :j].any() and not p[:, j + m:].any()
 
 
-def pin_vnc_worked_example():
-    """Alg. 2's m = 5 walkthrough (Sec. 3.2), values from tests/golden."""
+def pin_column_worked_example():
+    """The m = 5 walkthrough of Sec. 3.2 (column pair counts, the pairs of
+    column 4 in order, 25 pairs, where pair (2, 3) lands), values from
+    tests/golden."""
     gold = {}
-    with open(os.path.join(GOLDEN, "vnc_m5_worked_example.txt")) as f:
+    with open(os.path.join(GOLDEN, "column_pairs_m5_worked_example.txt")) as f:
         for ln in f:
             ln = ln.strip()
             if ln and not ln.startswith("#"):
                 k, *v = ln.split()
                 gold[k] = v
     m = 5
-    ia, jb, nc = oracle.vnc_pairs(m)
+    ia, jb, nc = oracle.column_pairs(m)
     assert nc.size == int(gold["columns"][0])
     assert list(nc) == [int(t) for t in gold["pairs_per_column"]]
     # num_pairs = min(c+1, m, 2m-1-c) is the same count
@@ -180,7 +182,7 @@ def pin_vnc_worked_example():
     b = np.zeros((1, m), np.uint32)
     a[0, 2] = 0x89ABCDEF
     b[0, 3] = 0xFEDCBA98
-    p = oracle.mul_vnc(a, b)
+    p = oracle.mul_columns(a, b)
     prod = 0x89ABCDEF * 0xFEDCBA98
     want = np.zeros(2 * m, np.uint32)
     want[5] = prod & 0xFFFFFFFF
@@ -289,9 +291,9 @@ def pin_closed_forms_variants():
         assert p[0] == 1 and not p[1:m].any() and p[m] == 0xFFFFFFFE and (p[m + 1:] == 0xFFFFFFFF).all()
 
 
-PINS = [pin_python_int_addsub, pin_python_int_mul, pin_python_int_mul_vnc,
+PINS = [pin_python_int_addsub, pin_python_int_mul, pin_python_int_mul_columns,
         pin_brute_force_small, pin_closed_forms, pin_invariants,
-        pin_vnc_worked_example, pin_ragged_and_mixed, pin_carry_probability,
+        pin_column_worked_example, pin_ragged_and_mixed, pin_carry_probability,
         pin_python_int_variants, pin_closed_forms_variants]
 
 
@@ -308,10 +310,11 @@ def test_bad_arguments_rejected():
     assert L.oracle_add(None, None, None, None, 0, 0) == 0
 
 
-def test_vnc_reports_unreachable_prepend():
-    """Alg. 2's Phase 5 leaves no carry for any m-limb inputs (2m-limb product)."""
+def test_columns_leave_no_carry_past_2m_limbs():
+    """The column form's carry pass ends with no carry for m-limb inputs (the
+    product has 2m limbs); the largest operands are the tightest case."""
     ones = np.full((3, 9), 0xFFFFFFFF, dtype=np.uint32)
-    oracle.mul_vnc(ones, ones)   # raises on a nonzero final carry
+    oracle.mul_columns(ones, ones)   # raises on a nonzero final carry
 
 
 def test_threaded_rows_match_single():
