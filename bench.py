@@ -14,6 +14,16 @@ host-buffer C-ABI entry points (copies in and out inside the timed region).
 ``--impl reference`` times the CPU oracle on the machine's host cores on a
 bounded sample of the same workload instead.
 
+The same line carries ``rows``: the other workloads -- the correctness mix
+(4096 x 1024-bit add, sub, mul), the batched multiply (2^16 pairs at 256 to
+8192 bits), the 200k-op ragged mixed batch (graph replay vs one launch per
+size) and the shared-operand product (tensor cores vs INT32) -- each timed
+call by call with L2 flushed before it, checked on every row against the
+oracle, reported against a measured peak (HBM copy and bf16 GEMM from
+MEASURED_PEAKS.json; integer-pipe ceilings from the libdotprobe
+microbenchmarks run in the same process), with the oracle's all-core time on
+the same rows and the clocks seen meanwhile.
+
 Multi-GPU: the ops are independent, so N ranks run N replicas of the step
 (weak scaling, no collective on the data path).
 """
@@ -296,6 +306,12 @@ def gpu_arm(args, rank, world, local):
     clocks = sampler.stop()
     e2e_ms = max_over_ranks(e2e_ms, world, dev)
 
+    rows = None
+    if rank == 0 and not args.no_rows:
+        rows = workload_rows(ctx, stream, local)
+    if world > 1:
+        torch.distributed.barrier()
+
     if rank == 0:
         hbm, src = peaks()
         dom = "add_short"
@@ -336,6 +352,7 @@ def gpu_arm(args, rank, world, local):
                     "ms_per_step": round(e2e_ms, 4), "api": "dot_add_host / dot_sub_host"},
             "gpu_launches": 4 * args.steps,
             "clocks": clocks,
+            "rows": rows,
         }
         print(json.dumps(out), flush=True)
     ctx.close()
@@ -450,18 +467,294 @@ def profile_case(args):
     print("profile case done")
 
 
-IMAD_PER_SM_CLK = 64   # 32-bit integer multiply-add lanes per SM per clock (FMA pipe)
+# ------------------------------------------------------------ workload rows
+# Every row below times its calls one by one with CUDA events on the calling
+# stream after writing a 256 MB buffer (twice the L2) on that stream and then
+# reading it back, so no call finds its inputs in L2 and none pays for writing
+# back the flush's dirty lines; checks every result against the oracle; and
+# times the oracle on all host cores on the same rows as the CPU baseline.
+L2_FLUSH_BYTES = 256 << 20
+L2_NOTE = "flushed before each timed call (256 MB written, then read back)"
+UNSATURATED_DIGIT_BITS = 27   # largest digit whose 64-bit column sums need no carry up to 512 limbs
 
 
-def int_peak():
-    """Nominal 32-bit IMAD rate (ops/s): SMs x 64 lanes x max SM clock."""
-    import torch
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
+def measured_peaks():
+    """HBM GB/s and dense bf16 TF/s (burst) from MEASURED_PEAKS.json, else the fallback figures."""
     try:
-        mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
     except Exception:
-        mhz = 2070.0
-    return sms * IMAD_PER_SM_CLK * mhz * 1e6, sms, mhz
+        return 6800.0, 1900.0, "fallback"
+
+
+class Timer:
+    """Cold-L2 CUDA-event timing of single calls on one stream."""
+
+    def __init__(self, stream):
+        import torch
+        self.stream = stream
+        self.flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def ms(self, fn, reps, warm=3):
+        import torch
+        for _ in range(warm):
+            fn()
+        ev = []
+        for _ in range(reps):
+            self.flush.zero_()
+            self.flush.sum()   # leaves L2 holding clean lines of the flush buffer
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            fn()
+            e1.record(self.stream)
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+        t = [a.elapsed_time(b) for a, b in ev]
+        return statistics.mean(t), statistics.median(t)
+
+
+def _cpu(fn, units, unit, sample):
+    """Time one oracle call on all host cores: (result, cpu_baseline dict)."""
+    import oracle
+    t0 = time.perf_counter()
+    res = fn(oracle.cores())
+    dt = time.perf_counter() - t0
+    return res, {"value": round(units / dt / 1e9, 6), "unit": unit, "cores": oracle.cores(), "kind": "oracle",
+                 "sample": sample, "seconds": round(dt, 3)}
+
+
+def _dv(x):
+    import torch
+    x = np.ascontiguousarray(x)
+    return torch.from_numpy(x.view(np.int32 if x.dtype == np.uint32 else np.int64)).cuda()
+
+
+def _hs(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def row_peaks():
+    """Integer-pipe ceilings measured on this GPU (libdotprobe)."""
+    from paper_2604_21566_gb300 import probe
+    return probe.measure()
+
+
+def _int_roofline(products, ms, pk):
+    pair = pk["mul_pair"]["per_s"]
+    mix = pk["colsum_r8"]["per_s"]
+    rate = products / (ms * 1e-3)
+    return {"bound": "alu", "achieved_products_per_s": round(rate, 1), "unit": "limb products/s",
+            "peak": round(pair, 1), "frac": round(rate / pair, 4),
+            "peak_source": "measured: mul.lo + mul.hi pair probe (libdotprobe)",
+            "peak_colsum_mix": round(mix, 1), "frac_of_colsum_mix": round(rate / mix, 4)}
+
+
+def row_c1(ctx, timer, pk, reps=100):
+    """Correctness mix: 4096 x 1024-bit add, sub and mul."""
+    import oracle
+    from paper_2604_21566_gb300 import dot
+    from paper_2604_21566_gb300 import workloads as W
+    import torch
+    hbm, _, src = measured_peaks()
+    d = W.correctness_mix()
+    n, m = d["x"].shape
+    a, b = _dv(d["x"]), _dv(d["y"])
+    asub, bsub = _dv(d["a_sub"]), _dv(d["b_sub"])
+    s = torch.empty_like(a)
+    c = torch.empty(n, dtype=torch.int32, device="cuda")
+    p = torch.empty((n, 2 * m), dtype=torch.int32, device="cuda")
+    floor = pk["launch_floor"]["us"]
+    out = {"workload": "4096 x 1024-bit pairs (m = 32): 50% uniform, 25% full-ripple all-ones, 25% sparse",
+           "l2": L2_NOTE, "ops": {}}
+    exact = True
+    cpu = {}
+    for name in ("add", "sub", "mul"):
+        if name == "add":
+            fn, x, y = (lambda: dot.add(a, b, s, c, ctx=ctx)), d["x"], d["y"]
+        elif name == "sub":
+            fn, x, y = (lambda: dot.sub(asub, bsub, s, c, ctx=ctx)), d["a_sub"], d["b_sub"]
+        else:
+            fn, x, y = (lambda: dot.mul(a, b, p, ctx=ctx)), d["x"], d["y"]
+        mean, med = timer.ms(fn, reps)
+        if name == "mul":
+            want, cpu[name] = _cpu(lambda t: oracle.mul(x, y, threads=t), n, "Gop/s", "all 4096 rows")
+            exact &= bool(np.array_equal(_hs(p), want))
+            roof = _int_roofline(n * m * m, mean, pk)
+        else:
+            f = oracle.add if name == "add" else oracle.sub
+            (ws, wc), cpu[name] = _cpu(lambda t: f(x, y, threads=t), n, "Gop/s", "all 4096 rows")
+            exact &= bool(np.array_equal(_hs(s), ws) and np.array_equal(_hs(c), wc))
+            gbs = n * (12 * m + 4) / (mean * 1e-3) / 1e9
+            roof = {"bound": "latency", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": round(gbs / hbm, 4), "peak_source": src,
+                    "launch_floor_us": floor, "frac_of_launch_floor": round(floor / (mean * 1e3), 4)}
+        out["ops"][name] = {"us": round(mean * 1e3, 2), "us_median": round(med * 1e3, 2),
+                            "gop_s": round(n / (mean * 1e-3) / 1e9, 4), "roofline": roof}
+    out["bit_exact"] = exact
+    out["bit_exact_rows"] = "all"
+    out["cpu_baseline"] = cpu
+    return out
+
+
+def row_c3(ctx, timer, pk, reps=20):
+    """Batched multiply at fixed size: 2^16 pairs at 256, 1024, 4096, 8192 bits."""
+    import oracle
+    from paper_2604_21566_gb300 import dot
+    from paper_2604_21566_gb300 import workloads as W
+    import torch
+    hbm, _, src = measured_peaks()
+    sizes = {}
+    exact = True
+    for m in W.BATCHED_MUL_SIZES:
+        x, y, _ = W.batched_mul(m)
+        n = x.shape[0]
+        a, b = _dv(x), _dv(y)
+        p = torch.empty((n, 2 * m), dtype=torch.int32, device="cuda")
+        mean, med = timer.ms(lambda: dot.mul(a, b, p, ctx=ctx), reps)
+        want, cpu = _cpu(lambda t: oracle.mul(x, y, threads=t), n, "Gop/s", f"all {n} rows")
+        ok = bool(np.array_equal(_hs(p), want))
+        exact &= ok
+        roof = _int_roofline(n * m * m, mean, pk)
+        gbs = n * 16 * m / (mean * 1e-3) / 1e9
+        roof["achieved_GB_s"] = round(gbs, 1)
+        roof["frac_hbm"] = round(gbs / hbm, 4)
+        roof["hbm_peak_source"] = src
+        if m <= 8:
+            roof["bound"] = "latency (too little work per launch for either pipe)"
+        sizes[f"{32 * m}_bit"] = {"m_limbs": m, "ops": n, "ms": round(mean, 4), "ms_median": round(med, 4),
+                                  "gop_s": round(n / (mean * 1e-3) / 1e9, 4),
+                                  "cols_per_lane": int(dot.plan(dot.OP_MUL, m, n).seg_limbs),
+                                  "roofline": roof, "bit_exact": ok, "cpu_baseline": cpu}
+        del a, b, p
+    return {"workload": "2^16 pairs at 256/1024/4096/8192 bits, uniform limbs + 10% both-all-ones pairs",
+            "l2": L2_NOTE, "bit_exact": exact, "bit_exact_rows": "all",
+            "sizes": sizes}
+
+
+def ragged_descriptors(w):
+    desc = np.zeros(w["op"].size, dtype=[("op", "<u4"), ("m", "<u4"), ("a_off", "<u8"), ("b_off", "<u8"),
+                                         ("r_off", "<u8")])
+    desc["op"], desc["m"] = w["op"], w["m"]
+    desc["a_off"] = desc["b_off"] = w["a_off"][:-1]
+    desc["r_off"] = w["r_off"][:-1]
+    return desc
+
+
+def row_c4(ctx, timer, pk, reps=10):
+    """Ragged mixed batch: one persistent bucketed kernel from a CUDA graph vs
+    one launch per (op, size)."""
+    import oracle
+    from paper_2604_21566_gb300 import dot
+    from paper_2604_21566_gb300 import workloads as W
+    import torch
+    w = W.ragged_mixed()
+    n = w["op"].size
+    desc = ragged_descriptors(w)
+    ddesc = torch.from_numpy(desc.view(np.uint8).copy()).cuda()
+    a, b = _dv(w["a"]), _dv(w["b"])
+    r = torch.zeros(int(w["r_off"][-1]), dtype=torch.int32, device="cuda")
+    cr = torch.zeros(n, dtype=torch.int32, device="cuda")
+    mean, med = timer.ms(lambda: dot.mixed_ragged(ddesc, a, b, r, cr, ctx=ctx), reps)
+    (wr, wc), cpu = _cpu(lambda t: oracle.mixed(desc["op"], desc["m"], desc["a_off"], desc["b_off"],
+                                                desc["r_off"], w["a"], w["b"], w["r_off"][-1], threads=t),
+                         n, "Gop/s", f"all {n} ops")
+    exact = bool(np.array_equal(_hs(r), wr) and np.array_equal(_hs(cr), wc))
+    # one launch per (op, size): operands regrouped contiguously beforehand
+    groups = []
+    for opc in (W.OP_ADD, W.OP_SUB, W.OP_MUL):
+        for m in np.unique(w["m"][w["op"] == opc]):
+            idx = np.nonzero((w["op"] == opc) & (w["m"] == m))[0]
+            lo = w["a_off"][idx].astype(np.int64)
+            sel = (lo[:, None] + np.arange(m)[None, :]).reshape(-1)
+            ga, gb = _dv(w["a"][sel].reshape(idx.size, m)), _dv(w["b"][sel].reshape(idx.size, m))
+            outw = 2 * m if opc == W.OP_MUL else m
+            groups.append((opc, ga, gb, torch.empty((idx.size, outw), dtype=torch.int32, device="cuda"),
+                           torch.empty(idx.size, dtype=torch.int32, device="cuda")))
+
+    def per_size():
+        for opc, ga, gb, go, gc in groups:
+            if opc == W.OP_MUL:
+                dot.mul(ga, gb, go, ctx=ctx)
+            elif opc == W.OP_ADD:
+                dot.add(ga, gb, go, gc, ctx=ctx)
+            else:
+                dot.sub(ga, gb, go, gc, ctx=ctx)
+    t_per, _ = timer.ms(per_size, 3, warm=1)
+    mulm = w["m"][w["op"] == W.OP_MUL].astype(np.int64)
+    prods = int((mulm ** 2).sum())
+    roof = _int_roofline(prods, mean, pk)
+    return {"workload": "200k ops, 30/30/40 add/sub/mul, log-uniform 128..16384 bits, shuffled",
+            "l2": L2_NOTE, "bit_exact": exact, "bit_exact_rows": "all",
+            "ms_persistent_graph": round(mean, 4), "ms_median": round(med, 4),
+            "gop_s": round(n / (mean * 1e-3) / 1e9, 4),
+            "ms_one_launch_per_size": round(t_per, 4), "launches_per_size": len(groups),
+            "speedup_vs_per_size": round(t_per / mean, 3), "mul_limb_products": prods,
+            "roofline": roof, "cpu_baseline": cpu}
+
+
+# 128 x 128 x 16 MMA units the Toeplitz kernel issues per tile of 128
+# operands at m = 64: per accumulator half one rank-one bias product at N = 256
+# (2 units) and 8 k-steps at N = 256 (16 units) plus 8 at N = 128 (8 units)
+TZ_UNITS_PER_TILE = 2 * (2 + 16 + 8)
+
+
+def row_c5(ctx, timer, pk, reps=50):
+    """Shared operand: one fixed 2048-bit multiplier x 2^16 2048-bit operands,
+    Toeplitz product on the tensor cores vs the INT32 paths."""
+    import oracle
+    from paper_2604_21566_gb300 import dot
+    from paper_2604_21566_gb300 import workloads as W
+    import torch
+    hbm, tc_peak, src = measured_peaks()
+    f, bb = W.shared_operand()
+    n, m = bb.shape
+    fa = np.ascontiguousarray(np.broadcast_to(f, bb.shape))
+    a, fd, b = _dv(fa), _dv(f), _dv(bb)
+    p = torch.empty((n, 2 * m), dtype=torch.int32, device="cuda")
+    want, cpu = _cpu(lambda t: oracle.mul(fa, bb, threads=t), n, "Gop/s", f"all {n} rows")
+    t_int, _ = timer.ms(lambda: dot.mul(a, b, p, ctx=ctx), reps)
+    ok = bool(np.array_equal(_hs(p), want))
+    t_sh, _ = timer.ms(lambda: dot.mul_shared(fd, b, p, tensor_cores=False, ctx=ctx), reps)
+    ok &= bool(np.array_equal(_hs(p), want))
+    t_tc, med = timer.ms(lambda: dot.mul_shared(fd, b, p, tensor_cores=True, ctx=ctx), reps)
+    ok &= bool(np.array_equal(_hs(p), want))
+    tiles = (n + 127) // 128
+    issued = 2.0 * 128 * 128 * 16 * TZ_UNITS_PER_TILE * tiles
+    useful = 2.0 * (4 * m) ** 2 * n
+    bytes_moved = n * 12 * m + 4 * m
+    tflops = issued / (t_tc * 1e-3) / 1e12
+    return {"workload": "fixed 2048-bit x 2^16 2048-bit (m = 64), uniform limbs",
+            "l2": L2_NOTE, "bit_exact": ok, "bit_exact_rows": "all",
+            "ms_tensor": round(t_tc, 4), "ms_tensor_median": round(med, 4), "ms_int32_batched": round(t_int, 4),
+            "ms_int32_shared": round(t_sh, 4), "speedup_tensor_vs_int32": round(t_int / t_tc, 3),
+            "gop_s_tensor": round(n / (t_tc * 1e-3) / 1e9, 4),
+            "roofline": {"bound": "tensor", "achieved": round(tflops, 1), "peak": tc_peak, "unit": "TFLOP/s",
+                         "frac": round(tflops / tc_peak, 4),
+                         "peak_source": f"{src} bf16 burst (fp16 runs at the bf16 rate)",
+                         "issued_units_128x128x16_per_tile": TZ_UNITS_PER_TILE,
+                         "useful_tflop_s": round(useful / (t_tc * 1e-3) / 1e12, 1),
+                         "frac_useful": round(useful / (t_tc * 1e-3) / 1e12 / tc_peak, 4),
+                         "achieved_GB_s": round(bytes_moved / (t_tc * 1e-3) / 1e9, 1),
+                         "frac_hbm": round(bytes_moved / (t_tc * 1e-3) / 1e9 / hbm, 4)},
+            "int32_roofline": _int_roofline(n * m * m, t_int, pk),
+            "cpu_baseline": cpu}
+
+
+def workload_rows(ctx, stream, local):
+    """The correctness-mix, batched-multiply, mixed-batch and shared-operand
+    rows of the default bench line, with the clocks seen while they ran."""
+    sampler = ClockSampler(local)
+    sampler.start()
+    timer = Timer(stream)
+    pk = row_peaks()
+    rows = {"int_peaks": pk,
+            "C1_correctness_mix": row_c1(ctx, timer, pk),
+            "C3_batched_mul": row_c3(ctx, timer, pk),
+            "C4_ragged_mixed": row_c4(ctx, timer, pk),
+            "C5_shared_operand": row_c5(ctx, timer, pk)}
+    rows["clocks"] = sampler.stop()
+    return rows
 
 
 def _event_ms(fn, reps, stream):
@@ -480,212 +773,78 @@ def _event_ms(fn, reps, stream):
 
 
 def suite(args):
-    """One JSON line per workload row: correctness mix, batched multiply per
-    size, mixed ragged batch vs one launch per size, shared-operand multiply."""
+    """One JSON line per row: the driver line's rows, then the further rows
+    (multiply at other sizes, squares, Karatsuba)."""
     import torch
     import oracle
     from paper_2604_21566_gb300 import dot
-    from paper_2604_21566_gb300 import workloads as W
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     ctx = dot.Context(0)
-    peak, sms, mhz = int_peak()
+    timer = Timer(stream)
+    pk = row_peaks()
 
-    def dv(x):
-        return torch.from_numpy(np.ascontiguousarray(x).view(
-            np.int32 if x.dtype == np.uint32 else np.int64)).cuda()
-
-    def hs(t):
-        return t.cpu().numpy().view(np.uint32)
-
-    def emit(d):
-        d["suite"] = True
-        print(json.dumps(d), flush=True)
+    def emit(name, d):
+        print(json.dumps({"suite": name, **d}), flush=True)
 
     def want(name):
         return not args.only or name in args.only.split(",")
 
+    emit("int_peaks", pk)
     if want("mix"):
-        # -- correctness mix: 4096 x 1024-bit, latency-bound
-        d = W.correctness_mix()
-        a, b = dv(d["x"]), dv(d["y"])
-        asub, bsub = dv(d["a_sub"]), dv(d["b_sub"])
-        s = torch.empty_like(a)
-        c = torch.empty(a.shape[0], dtype=torch.int32, device="cuda")
-        p = torch.empty((a.shape[0], 64), dtype=torch.int32, device="cuda")
-        t_add = _event_ms(lambda: dot.add(a, b, s, c, ctx=ctx), 200, stream)
-        ok = np.array_equal(hs(s), oracle.add(d["x"], d["y"])[0])
-        t_sub = _event_ms(lambda: dot.sub(asub, bsub, s, c, ctx=ctx), 200, stream)
-        ok &= np.array_equal(hs(s), oracle.sub(d["a_sub"], d["b_sub"])[0])
-        t_mul = _event_ms(lambda: dot.mul(a, b, p, ctx=ctx), 200, stream)
-        ok &= np.array_equal(hs(p), oracle.mul(d["x"], d["y"], threads=oracle.cores()))
-        emit({"workload": "correctness mix: 4096 x 1024-bit (m=32), add/sub/mul", "bit_exact": bool(ok),
-              "us_per_call": {"add": round(t_add * 1e3, 2), "sub": round(t_sub * 1e3, 2),
-                              "mul": round(t_mul * 1e3, 2)},
-              "gop_s": {"add": round(4096 / t_add / 1e6, 3), "sub": round(4096 / t_sub / 1e6, 3),
-                        "mul": round(4096 / t_mul / 1e6, 3)}})
-
+        emit("C1_correctness_mix", row_c1(ctx, timer, pk))
     if want("mul"):
-        # -- batched multiply at fixed size
-        rows = []
-        for m in W.BATCHED_MUL_SIZES:
-            x, y, _ = W.batched_mul(m)
-            a, b = dv(x), dv(y)
-            p = torch.empty((x.shape[0], 2 * m), dtype=torch.int32, device="cuda")
-            ms = _event_ms(lambda: dot.mul(a, b, p, ctx=ctx), 20, stream)
-            sel = np.random.default_rng(m).integers(0, x.shape[0], 512)
-            ok = np.array_equal(hs(p)[sel], oracle.mul(x[sel], y[sel]))
-            prods = x.shape[0] * m * m
-            imad = 2.0 * prods / (ms * 1e-3)
-            rows.append({"m_limbs": m, "bits": 32 * m, "ops": x.shape[0], "ms": round(ms, 4),
-                         "gop_s": round(x.shape[0] / (ms * 1e-3) / 1e9, 4),
-                         "tera_limb_products_s": round(prods / (ms * 1e-3) / 1e12, 3),
-                         "GB_s": round(16 * m * x.shape[0] / (ms * 1e-3) / 1e9, 1),
-                         "roofline": {"bound": "alu", "achieved_imad_per_s": imad, "peak": peak,
-                                      "frac": round(imad / peak, 4)},
-                         "bit_exact_sample": bool(ok)})
-        emit({"workload": "batched multiply: 2^16 pairs at 256/1024/4096/8192 bits",
-              "int_peak": {"imad_per_s": peak, "sms": sms, "sm_mhz": mhz,
-                           "per_sm_clk": IMAD_PER_SM_CLK, "algorithmic_imad_per_product": 2},
-              "sizes": rows})
-
+        emit("C3_batched_mul", row_c3(ctx, timer, pk))
+    if want("mixed"):
+        emit("C4_ragged_mixed", row_c4(ctx, timer, pk))
+    if want("shared"):
+        emit("C5_shared_operand", row_c5(ctx, timer, pk))
     if want("mulx"):
-        # -- batched multiply between and above the workload's sizes: one size
+        # batched multiply between and above the workload's sizes: one size
         # for each further column shape (12 columns on 16 lanes, 12 on 25, 16)
+        from paper_2604_21566_gb300 import workloads as W
         rows = []
         for m in (192, 300, 512):
             x, y, _ = W.batched_mul(m)
-            a, b = dv(x), dv(y)
+            a, b = _dv(x), _dv(y)
             p = torch.empty((x.shape[0], 2 * m), dtype=torch.int32, device="cuda")
-            ms = _event_ms(lambda: dot.mul(a, b, p, ctx=ctx), 20, stream)
+            ms, _ = timer.ms(lambda: dot.mul(a, b, p, ctx=ctx), 10)
             sel = np.random.default_rng(m).integers(0, x.shape[0], 256)
-            ok = np.array_equal(hs(p)[sel], oracle.mul(x[sel], y[sel], threads=oracle.cores()))
-            prods = x.shape[0] * m * m
-            imad = 2.0 * prods / (ms * 1e-3)
+            ok = np.array_equal(_hs(p)[sel], oracle.mul(x[sel], y[sel], threads=oracle.cores()))
             rows.append({"m_limbs": m, "bits": 32 * m, "ops": x.shape[0], "ms": round(ms, 4),
                          "cols_per_lane": dot.plan(dot.OP_MUL, m, x.shape[0]).seg_limbs,
-                         "tera_limb_products_s": round(prods / (ms * 1e-3) / 1e12, 3),
-                         "roofline": {"bound": "alu", "achieved_imad_per_s": imad, "peak": peak,
-                                      "frac": round(imad / peak, 4)},
-                         "bit_exact_sample": bool(ok)})
-        emit({"workload": "batched multiply: 2^16 pairs at 6144/9600/16384 bits", "sizes": rows})
-
+                         "roofline": _int_roofline(x.shape[0] * m * m, ms, pk), "bit_exact_sample": bool(ok)})
+        emit("batched_mul_other_sizes", {"workload": "2^16 pairs at 6144/9600/16384 bits", "sizes": rows})
     if want("sqr"):
-        # -- batched square (half the partial products) vs the general product
+        from paper_2604_21566_gb300 import workloads as W
         rows = []
         for m in (32, 128, 256):
             x, _, _ = W.batched_mul(m)
-            a = dv(x)
+            a = _dv(x)
             p = torch.empty((x.shape[0], 2 * m), dtype=torch.int32, device="cuda")
-            t_mul = _event_ms(lambda: dot.mul(a, a, p, ctx=ctx), 20, stream)
-            t_sqr = _event_ms(lambda: dot.sqr(a, p, ctx=ctx), 20, stream)
+            t_mul, _ = timer.ms(lambda: dot.mul(a, a, p, ctx=ctx), 10)
+            t_sqr, _ = timer.ms(lambda: dot.sqr(a, p, ctx=ctx), 10)
             sel = np.random.default_rng(m).integers(0, x.shape[0], 512)
-            ok = np.array_equal(hs(p)[sel], oracle.sqr(x[sel]))
+            ok = np.array_equal(_hs(p)[sel], oracle.sqr(x[sel]))
             rows.append({"m_limbs": m, "ops": x.shape[0], "ms_mul": round(t_mul, 4), "ms_sqr": round(t_sqr, 4),
                          "speedup_sqr_vs_mul": round(t_mul / t_sqr, 3), "bit_exact_sample": bool(ok)})
-        emit({"workload": "batched square: 2^16 operands at 1024/4096/8192 bits", "sizes": rows})
-
+        emit("batched_square", {"workload": "2^16 operands at 1024/4096/8192 bits", "sizes": rows})
     if want("kara"):
-        # -- Karatsuba above the base case: effective schoolbook limb products per second
         rows = []
         for m, batch in ((1024, 4096), (2048, 2048), (4096, 1024), (8192, 256)):
             g = np.random.default_rng(5000 + m)
             x = g.integers(0, 2 ** 32, (batch, m), dtype=np.uint64).astype(np.uint32)
             y = g.integers(0, 2 ** 32, (batch, m), dtype=np.uint64).astype(np.uint32)
-            a, b = dv(x), dv(y)
+            a, b = _dv(x), _dv(y)
             p = torch.empty((batch, 2 * m), dtype=torch.int32, device="cuda")
-            ms = _event_ms(lambda: dot.mul_karatsuba(a, b, p, ctx=ctx), 5, stream)
+            ms, _ = timer.ms(lambda: dot.mul_karatsuba(a, b, p, ctx=ctx), 5)
             sel = np.arange(0, batch, max(1, batch // 4))
-            ok = np.array_equal(hs(p)[sel], oracle.mul(x[sel], y[sel], threads=8))
-            prods = batch * m * m
+            ok = np.array_equal(_hs(p)[sel], oracle.mul(x[sel], y[sel], threads=8))
             rows.append({"m_limbs": m, "bits": 32 * m, "ops": batch, "ms": round(ms, 4),
-                         "gop_s": round(batch / (ms * 1e-3) / 1e9, 6),
-                         "schoolbook_equiv_tera_products_s": round(prods / (ms * 1e-3) / 1e12, 3),
+                         "schoolbook_equiv_tera_products_s": round(batch * m * m / (ms * 1e-3) / 1e12, 3),
                          "bit_exact_sample": bool(ok)})
-        emit({"workload": "Karatsuba above 512 limbs: 32k..262k-bit products",
-              "note": "schoolbook-equivalent rate = batch m^2 / time (m^2 products a schoolbook would do)",
-              "sizes": rows})
-
-    if want("mixed"):
-        # -- mixed ragged batch: one persistent bucketed kernel vs one launch per size
-        w = W.ragged_mixed()
-        n = w["op"].size
-        desc = np.zeros(n, dtype=[("op", "<u4"), ("m", "<u4"), ("a_off", "<u8"), ("b_off", "<u8"),
-                                  ("r_off", "<u8")])
-        desc["op"], desc["m"] = w["op"], w["m"]
-        desc["a_off"] = desc["b_off"] = w["a_off"][:-1]
-        desc["r_off"] = w["r_off"][:-1]
-        ddesc = torch.from_numpy(desc.view(np.uint8).copy()).cuda()
-        a, b = dv(w["a"]), dv(w["b"])
-        r = torch.zeros(int(w["r_off"][-1]), dtype=torch.int32, device="cuda")
-        cr = torch.zeros(n, dtype=torch.int32, device="cuda")
-        t_mixed = _event_ms(lambda: dot.mixed_ragged(ddesc, a, b, r, cr, ctx=ctx), 20, stream)
-        wr, wc = oracle.mixed(desc["op"], desc["m"], desc["a_off"], desc["b_off"], desc["r_off"],
-                              w["a"], w["b"], w["r_off"][-1])
-        ok = np.array_equal(hs(r), wr) and np.array_equal(hs(cr), wc)
-        # one launch per (op, size): operands regrouped contiguously beforehand
-        groups = []
-        for opc in (W.OP_ADD, W.OP_SUB, W.OP_MUL):
-            for m in np.unique(w["m"][w["op"] == opc]):
-                idx = np.nonzero((w["op"] == opc) & (w["m"] == m))[0]
-                rows_a = np.stack([w["a"][int(w["a_off"][i]):int(w["a_off"][i]) + m] for i in idx])
-                rows_b = np.stack([w["b"][int(w["a_off"][i]):int(w["a_off"][i]) + m] for i in idx])
-                ga, gb = dv(rows_a), dv(rows_b)
-                out = torch.empty((idx.size, 2 * m if opc == W.OP_MUL else m), dtype=torch.int32,
-                                  device="cuda")
-                gc = torch.empty(idx.size, dtype=torch.int32, device="cuda")
-                groups.append((opc, ga, gb, out, gc))
-
-        def per_size():
-            for opc, ga, gb, out, gc in groups:
-                if opc == W.OP_MUL:
-                    dot.mul(ga, gb, out, ctx=ctx)
-                elif opc == W.OP_ADD:
-                    dot.add(ga, gb, out, gc, ctx=ctx)
-                else:
-                    dot.sub(ga, gb, out, gc, ctx=ctx)
-        t_per = _event_ms(per_size, 5, stream)
-        prods = int((w["m"][w["op"] == W.OP_MUL].astype(np.int64) ** 2).sum())
-        emit({"workload": "ragged mixed: 200k ops, 30/30/40 add/sub/mul, 128..16384 bits",
-              "bit_exact": bool(ok), "ms_persistent_graph": round(t_mixed, 4),
-              "gop_s": round(n / (t_mixed * 1e-3) / 1e9, 4),
-              "ms_one_launch_per_size": round(t_per, 4), "launches_per_size": len(groups),
-              "speedup_vs_per_size": round(t_per / t_mixed, 3),
-              "roofline": {"bound": "alu", "achieved_imad_per_s": 2.0 * prods / (t_mixed * 1e-3),
-                           "peak": peak, "frac": round(2.0 * prods / (t_mixed * 1e-3) / peak, 4)}})
-
-    if want("shared"):
-        # -- shared operand: Toeplitz product on the tensor cores vs the INT32 paths
-        f, bb = W.shared_operand()
-        n = bb.shape[0]
-        a = dv(np.ascontiguousarray(np.broadcast_to(f, bb.shape)))
-        fd, b = dv(f), dv(bb)
-        p = torch.empty((n, 128), dtype=torch.int32, device="cuda")
-        sel = np.arange(0, n, 97)
-        want = oracle.mul(np.broadcast_to(f, (sel.size, 64)), bb[sel])
-        t_int = _event_ms(lambda: dot.mul(a, b, p, ctx=ctx), 50, stream)
-        ok = np.array_equal(hs(p)[sel], want)
-        t_int_sh = _event_ms(lambda: dot.mul_shared(fd, b, p, tensor_cores=False, ctx=ctx), 50, stream)
-        ok &= np.array_equal(hs(p)[sel], want)
-        t_tc = _event_ms(lambda: dot.mul_shared(fd, b, p, tensor_cores=True, ctx=ctx), 50, stream)
-        ok &= np.array_equal(hs(p)[sel], want)
-        # tensor work issued: 48 MMAs of 128 x 128 x 16 per 128 operands
-        flops = 2.0 * 128 * 128 * 16 * 48 * ((n + 127) // 128)
-        useful = 2.0 * 256 * 256 * n
-        hbm, _ = peaks()
-        tc_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"] \
-            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
-        bytes_moved = n * (256 + 512) + 256
-        emit({"workload": "shared operand: fixed 2048-bit x 2^16 2048-bit", "bit_exact_sample": bool(ok),
-              "ms_int32_batched": round(t_int, 4), "ms_int32_shared": round(t_int_sh, 4),
-              "ms_tensor": round(t_tc, 4), "speedup_tensor_vs_int32": round(t_int / t_tc, 3),
-              "gop_s_tensor": round(n / (t_tc * 1e-3) / 1e9, 4),
-              "roofline_tensor": {"issued_tflop_s": round(flops / (t_tc * 1e-3) / 1e12, 1),
-                                  "useful_tflop_s": round(useful / (t_tc * 1e-3) / 1e12, 1),
-                                  "peak_fp16_tflop_s": tc_peak,
-                                  "frac_issued": round(flops / (t_tc * 1e-3) / 1e12 / tc_peak, 4),
-                                  "GB_s": round(bytes_moved / (t_tc * 1e-3) / 1e9, 1),
-                                  "frac_hbm": round(bytes_moved / (t_tc * 1e-3) / 1e9 / hbm, 4)}})
+        emit("karatsuba", {"workload": "Karatsuba above 512 limbs: 32k..262k-bit products",
+                           "note": "schoolbook-equivalent rate = batch m^2 / time", "sizes": rows})
     assert ctx.check() == dot.OK
     ctx.close()
 
@@ -697,7 +856,7 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run only the small ncu case of the dominant kernel")
     ap.add_argument("--launches", type=int, default=3)
-    ap.add_argument("--only", default="", help="--suite rows to run: mix,mul,mulx,sqr,kara,mixed,shared")
+    ap.add_argument("--only", default="", help="--suite rows to run: mix,mul,mixed,shared,mulx,sqr,kara")
     ap.add_argument("--case", choices=["add", "long", "mul", "shared"], default="add",
                     help="which kernel --profile-case runs")
     ap.add_argument("--gpus", type=int, default=1)
@@ -706,6 +865,8 @@ def main():
     ap.add_argument("--impl", choices=["dot", "reference"], default="dot")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    ap.add_argument("--no-rows", action="store_true",
+                    help="skip the correctness-mix, multiply, mixed-batch and shared-operand rows")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -254,8 +254,10 @@ def mul_ragged(a, b, off):
     return p, poff
 
 
-def mixed(op, m, a_off, b_off, r_off, a, b, r_len_total):
-    """Mixed ragged batch: returns (r, carry)."""
+def mixed(op, m, a_off, b_off, r_off, a, b, r_len_total, threads: int = 1):
+    """Mixed ragged batch: returns (r, carry).  With threads > 1 the ops are
+    split into contiguous ranges, one per host thread; every op writes only
+    its own result range and carry slot."""
     op, m = _c(op), _c(m)
     a_off, b_off, r_off = _c(a_off, np.uint64), _c(b_off, np.uint64), _c(r_off, np.uint64)
     a, b = _c(a), _c(b)
@@ -263,8 +265,21 @@ def mixed(op, m, a_off, b_off, r_off, a, b, r_len_total):
     r = np.zeros(int(r_len_total), dtype=np.uint32)
     # a sentinel, so that a carry slot the oracle failed to write shows
     c = np.full(n, 0xFFFFFFFF, dtype=np.uint32)
-    _check(lib().oracle_mixed(_p32(op), _p32(m), _p64(a_off), _p64(b_off), _p64(r_off), n,
-                              _p32(a), _p32(b), _p32(r), _p32(c)), "oracle_mixed")
+    L = lib()
+
+    def call(lo, hi):
+        return L.oracle_mixed(_p32(op[lo:hi]), _p32(m[lo:hi]), _p64(a_off[lo:hi]), _p64(b_off[lo:hi]),
+                              _p64(r_off[lo:hi]), hi - lo, _p32(a), _p32(b), _p32(r), _p32(c[lo:hi]))
+
+    workers = max(1, min(threads, n))
+    if workers == 1:
+        _check(call(0, n), "oracle_mixed")
+        return r, c
+    step = (n + workers - 1) // workers
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        rcs = list(ex.map(lambda lo: call(lo, min(n, lo + step)), range(0, n, step)))
+    for rc in rcs:
+        _check(rc, "oracle_mixed")
     return r, c
 
 

@@ -2,7 +2,9 @@
 
 Each .cu file under csrc/ is compiled by nvcc in parallel into _build/, then
 linked into paper_2604_21566_gb300/libdot.so with the CUDA runtime linked
-statically.  Rebuilds only what changed.
+statically.  The microbenchmarks under csrc/probe/ (the peaks the bench
+reports kernels against; no arithmetic of the library) are linked into
+libdotprobe.so the same way.  Rebuilds only what changed.
 """
 from __future__ import annotations
 
@@ -18,6 +20,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdot.so")
+PROBE_LIB = os.path.join(PKG, "libdotprobe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
          "-I", INCLUDE, "-I", CSRC]
@@ -30,8 +33,8 @@ def nvcc() -> str:
     return p
 
 
-def _sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+def _sources(sub: str = ""):
+    return sorted(glob.glob(os.path.join(CSRC, sub, "*.cu")))
 
 
 def _headers():
@@ -47,18 +50,21 @@ def _stale(target, deps):
 
 
 def build(verbose: bool = False, extra_flags=None, jobs: int | None = None) -> str:
+    """Build libdot.so and libdotprobe.so; returns the path of libdot.so."""
     os.makedirs(BUILD, exist_ok=True)
     nv = nvcc()
     hdrs = _headers()
-    srcs = _sources()
     flags = FLAGS + list(extra_flags or [])
-    objs = []
+    libs = ((LIB, _sources(), ""), (PROBE_LIB, _sources("probe"), "probe_"))
     todo = []
-    for src in srcs:
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        objs.append(obj)
-        if _stale(obj, [src] + hdrs):
-            todo.append((src, obj))
+    objs = {}
+    for lib, srcs, prefix in libs:
+        objs[lib] = []
+        for src in srcs:
+            obj = os.path.join(BUILD, prefix + os.path.basename(src)[:-3] + ".o")
+            objs[lib].append(obj)
+            if _stale(obj, [src] + hdrs):
+                todo.append((src, obj))
 
     def compile_one(job):
         src, obj = job
@@ -75,13 +81,14 @@ def build(verbose: bool = False, extra_flags=None, jobs: int | None = None) -> s
             for msg in ex.map(compile_one, todo):
                 if verbose and msg:
                     print(msg)
-    if todo or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nv, *ARCH, "-shared", "-o", tmp, *objs]
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError(f"link of libdot.so failed:\n{r.stderr}")
-        os.replace(tmp, LIB)
+    for lib, _, _ in libs:
+        if todo or _stale(lib, objs[lib]):
+            tmp = lib + f".tmp{os.getpid()}"
+            cmd = [nv, *ARCH, "-shared", "-o", tmp, *objs[lib]]
+            r = subprocess.run(cmd, capture_output=True, text=True)
+            if r.returncode != 0:
+                raise RuntimeError(f"link of {os.path.basename(lib)} failed:\n{r.stderr}")
+            os.replace(tmp, lib)
     return LIB
 
 

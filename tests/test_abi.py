@@ -82,3 +82,20 @@ def test_mul_columns_fill_the_warp():
     with pytest.raises(dot.DotError):
         dot.plan(7, 4, 1)
     assert dot.plan(dot.OP_ADD, 4, 0).kernel == 0
+
+
+def test_probe_library_exports():
+    """libdotprobe (the bench's integer-pipe microbenchmarks) builds and
+    exports what include/dot_probe.h declares."""
+    import os
+    import re
+    B.build()
+    lib = ctypes.CDLL(os.path.join(os.path.dirname(B.__file__), "libdotprobe.so"))
+    hdr = open(os.path.join(B.INCLUDE, "dot_probe.h")).read()
+    names = re.findall(r"DOTP_API\s+[\w\s\*]*?\b(dotp_\w+)\s*\(", hdr)
+    assert set(names) == {"dotp_run", "dotp_occupancy"}
+    for n in names:
+        assert hasattr(lib, n), n
+    # argument checks need no GPU
+    ms, units = ctypes.c_float(), ctypes.c_double()
+    assert lib.dotp_run(99, 1, 32, 1, 1, ctypes.byref(ms), ctypes.byref(units)) == 1000
