@@ -13,6 +13,9 @@
 //  * Phases 3-4 (adding the carries back) happen in registers before the
 //    streaming store.
 // Subtraction is the same with borrows (Sec. 3.1, "Subtraction").
+#include <atomic>
+#include <mutex>
+
 #include "dot_internal.cuh"
 #include "dot_plan.h"
 #include "dot_addsub.cuh"
@@ -575,7 +578,8 @@ template <bool SUB>
 static dot_status_t addsub_batched(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b, uint32_t *s,
                                    uint32_t *cout, size_t m, size_t batch, cudaStream_t st)
 {
-    dot_status_t rc = dot_check_ctx(ctx);
+    DeviceScope scope;
+    dot_status_t rc = dot_check_ctx(ctx, scope);
     if (rc != DOT_OK) return rc;
     if (batch == 0) return DOT_OK;
     if (!cout) return DOT_EINVAL;
@@ -605,7 +609,8 @@ template <bool SUB>
 static dot_status_t addsub_ragged(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b, uint32_t *s,
                                   uint32_t *cout, const uint64_t *off, size_t batch, cudaStream_t st)
 {
-    dot_status_t rc = dot_check_ctx(ctx);
+    DeviceScope scope;
+    dot_status_t rc = dot_check_ctx(ctx, scope);
     if (rc != DOT_OK) return rc;
     if (batch == 0) return DOT_OK;
     if (!a || !b || !s || !cout || !off) return DOT_EINVAL;
@@ -621,7 +626,8 @@ template <bool SUB>
 static dot_status_t addsub_general(dot_ctx_t ctx, const uint32_t *a, size_t ma, const uint32_t *b, size_t mb,
                                    const uint32_t *cin, uint32_t *s, uint32_t *cout, size_t batch, cudaStream_t st)
 {
-    dot_status_t rc = dot_check_ctx(ctx);
+    DeviceScope scope;
+    dot_status_t rc = dot_check_ctx(ctx, scope);
     if (rc != DOT_OK) return rc;
     if (batch == 0) return DOT_OK;
     if (mb > ma || !cout) return DOT_EINVAL;
@@ -729,19 +735,34 @@ DOT_API dot_status_t dot_sub_unequal(dot_ctx_t ctx, const uint32_t *a, size_t ma
 static __device__ __align__(256) unsigned long long
     g_noalloc_scratch[DOT_NOALLOC_HDR + DOT_NOALLOC_MAX_TILES];
 
-// device address of g_noalloc_scratch, looked up once per device
-static unsigned long long *g_noalloc_addr[DOT_NOALLOC_MAX_DEVICES];
+// Device address of g_noalloc_scratch and the SM count, looked up once per
+// device and published for every host thread: a reader that sees the address
+// (acquire) also sees the SM count written before it (release); the lookup
+// itself runs under a lock, so concurrent first calls look it up once.
+static std::atomic<unsigned long long *> g_noalloc_addr[DOT_NOALLOC_MAX_DEVICES];
 static int g_noalloc_sms[DOT_NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_lock;
 
-static dot_status_t noalloc_setup(int device)
+// The caller has made `device` current.
+static dot_status_t noalloc_setup(int device, unsigned long long **addr, int *sms)
 {
-    if (g_noalloc_addr[device]) return DOT_OK;
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return DOT_ECUDA;
-    int sms = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return DOT_ECUDA;
-    g_noalloc_sms[device] = sms;
-    g_noalloc_addr[device] = (unsigned long long *)p;
+    unsigned long long *p = g_noalloc_addr[device].load(std::memory_order_acquire);
+    if (!p) {
+        std::lock_guard<std::mutex> guard(g_noalloc_lock);
+        p = g_noalloc_addr[device].load(std::memory_order_relaxed);
+        if (!p) {
+            void *sym = nullptr;
+            int n = 0;
+            if (cudaGetSymbolAddress(&sym, g_noalloc_scratch) != cudaSuccess || !sym) return DOT_ECUDA;
+            if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n < 1)
+                return DOT_ECUDA;
+            g_noalloc_sms[device] = n;
+            p = (unsigned long long *)sym;
+            g_noalloc_addr[device].store(p, std::memory_order_release);
+        }
+    }
+    *addr = p;
+    *sms = g_noalloc_sms[device];
     return DOT_OK;
 }
 
@@ -811,15 +832,15 @@ extern "C" DOT_API dot_status_t dot_add_noalloc(int device, const uint32_t *a, c
     if (pl.kernel == DOT_K_ADDSUB_TILE && (pl.tiles > DOT_NOALLOC_MAX_TILES ||
                                            batch > DOT_NOALLOC_MAX_TILES / pl.tiles))
         return DOT_EUNSUPPORTED;   // more tiles than the fixed scratch array holds
-    int cur = -1;
-    if (cudaGetDevice(&cur) != cudaSuccess) return DOT_ECUDA;
-    if (cur != device && cudaSetDevice(device) != cudaSuccess) return DOT_ECUDA;
-    rc = noalloc_setup(device);
+    // the caller's device is put back on every return path
+    DeviceScope scope;
+    if (scope.enter(device) != DOT_OK) return DOT_ECUDA;
+    unsigned long long *scratch = nullptr;
+    int sms = 0;
+    rc = noalloc_setup(device, &scratch, &sms);
     if (rc != DOT_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     if (m == 0) return cudaMemsetAsync(carry_out, 0, batch * 4, st) == cudaSuccess ? DOT_OK : DOT_ECUDA;
-    return vec ? noalloc_launch<false, 4>(g_noalloc_sms[device], g_noalloc_addr[device], pl, a, b, s,
-                                          carry_out, m, batch, st)
-               : noalloc_launch<false, 1>(g_noalloc_sms[device], g_noalloc_addr[device], pl, a, b, s,
-                                          carry_out, m, batch, st);
+    return vec ? noalloc_launch<false, 4>(sms, scratch, pl, a, b, s, carry_out, m, batch, st)
+               : noalloc_launch<false, 1>(sms, scratch, pl, a, b, s, carry_out, m, batch, st);
 }

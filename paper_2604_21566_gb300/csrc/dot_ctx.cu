@@ -5,18 +5,10 @@
 #include "dot_internal.cuh"
 #include "dot_plan.h"
 
-static dot_status_t set_device(int device)
-{
-    int cur = -1;
-    if (cudaGetDevice(&cur) != cudaSuccess) return DOT_ECUDA;
-    if (cur != device && cudaSetDevice(device) != cudaSuccess) return DOT_ECUDA;
-    return DOT_OK;
-}
-
-dot_status_t dot_check_ctx(dot_ctx_t ctx)
+dot_status_t dot_check_ctx(dot_ctx_t ctx, DeviceScope &scope)
 {
     if (!ctx) return DOT_EINVAL;
-    return set_device(ctx->device);
+    return scope.enter(ctx->device);
 }
 
 int dot_blocks_per_sm(const void *kernel, int threads, size_t smem)
@@ -50,7 +42,8 @@ DOT_API dot_status_t dot_ctx_create(dot_ctx_t *out, int device)
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess) return DOT_ECUDA;
     if (device < 0 || device >= ndev) return DOT_EINVAL;
-    if (set_device(device) != DOT_OK) return DOT_ECUDA;
+    DeviceScope scope;
+    if (scope.enter(device) != DOT_OK) return DOT_ECUDA;
     dot_ctx_t c = (dot_ctx_t)calloc(1, sizeof(struct dot_ctx));
     if (!c) return DOT_ENOMEM;
     c->device = device;
@@ -92,7 +85,8 @@ DOT_API dot_status_t dot_ctx_create(dot_ctx_t *out, int device)
 DOT_API void dot_ctx_destroy(dot_ctx_t c)
 {
     if (!c) return;
-    set_device(c->device);
+    DeviceScope scope;
+    scope.enter(c->device);
     cudaDeviceSynchronize();
     dot_mixed_release(c);
     for (int i = 0; i < 8; ++i)
@@ -109,7 +103,8 @@ DOT_API void dot_ctx_destroy(dot_ctx_t c)
 
 DOT_API dot_status_t dot_ctx_check(dot_ctx_t c, dot_stream_t stream)
 {
-    dot_status_t st = dot_check_ctx(c);
+    DeviceScope scope;
+    dot_status_t st = dot_check_ctx(c, scope);
     if (st != DOT_OK) return st;
     if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return DOT_ECUDA;
     uint32_t h = 0;

@@ -33,7 +33,8 @@ static size_t round16(size_t x) { return (x + 15) & ~(size_t)15; }
 static dot_status_t host_run(dot_ctx_t c, int op, const uint32_t *a, const uint32_t *b, uint32_t *r,
                              uint32_t *cout, size_t m, size_t batch, cudaStream_t user)
 {
-    dot_status_t rc = dot_check_ctx(c);
+    DeviceScope scope;
+    dot_status_t rc = dot_check_ctx(c, scope);
     if (rc != DOT_OK) return rc;
     if (batch == 0) return DOT_OK;
     const bool mul = op == DOT_OP_MUL;

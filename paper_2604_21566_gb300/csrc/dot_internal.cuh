@@ -250,8 +250,36 @@ __device__ __forceinline__ void gp_compose(uint32_t &g, uint32_t &p, uint32_t g_
 }
 
 // ------------------------------------------------------------ host helpers
+// Makes a CUDA device current for the lifetime of the object and puts the
+// caller's device back when it goes out of scope, so that no entry point
+// leaves the calling thread on another device.  Kernels launched meanwhile
+// keep running on the device they were launched on.
+class DeviceScope {
+  public:
+    DeviceScope() = default;
+    DeviceScope(const DeviceScope &) = delete;
+    DeviceScope &operator=(const DeviceScope &) = delete;
+    ~DeviceScope()
+    {
+        if (prev_ >= 0) cudaSetDevice(prev_);
+    }
+    dot_status_t enter(int device)
+    {
+        int cur = -1;
+        if (cudaGetDevice(&cur) != cudaSuccess) return DOT_ECUDA;
+        if (cur == device) return DOT_OK;
+        if (cudaSetDevice(device) != cudaSuccess) return DOT_ECUDA;
+        if (prev_ < 0) prev_ = cur;
+        return DOT_OK;
+    }
+
+  private:
+    int prev_ = -1;   // device to restore, or -1 when nothing was switched
+};
+
 dot_status_t dot_lookback_prepare(dot_ctx_t ctx, size_t tiles, LookbackArgs *out);
-dot_status_t dot_check_ctx(dot_ctx_t ctx);
+// validates ctx and makes its device current for the lifetime of `scope`
+dot_status_t dot_check_ctx(dot_ctx_t ctx, DeviceScope &scope);
 int dot_blocks_per_sm(const void *kernel, int threads, size_t smem);
 
 // ranges [p, p + n) overlap partially (not identical, not disjoint)

@@ -340,7 +340,8 @@ DOT_API dot_status_t dot_mixed_ragged(dot_ctx_t ctx, const dot_desc_t *desc, siz
                                       const uint32_t *a, const uint32_t *b, uint32_t *r,
                                       uint32_t *carry, dot_stream_t stream)
 {
-    dot_status_t rc = dot_check_ctx(ctx);
+    DeviceScope scope;
+    dot_status_t rc = dot_check_ctx(ctx, scope);
     if (rc != DOT_OK) return rc;
     if (nops == 0) return DOT_OK;
     if (!desc || !a || !b || !r || !carry || nops >= MIX_MAX_OPS) return DOT_EINVAL;

@@ -162,7 +162,8 @@ extern "C" {
 DOT_API dot_status_t dot_mul(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b, uint32_t *p, size_t m,
                              size_t batch, dot_stream_t stream)
 {
-    dot_status_t rc = dot_check_ctx(ctx);
+    DeviceScope scope;
+    dot_status_t rc = dot_check_ctx(ctx, scope);
     if (rc != DOT_OK) return rc;
     if (batch == 0 || m == 0) return DOT_OK;
     if (m > DOT_MUL_MAX_LIMBS) return DOT_EUNSUPPORTED;
@@ -185,7 +186,8 @@ DOT_API dot_status_t dot_mul(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b
 DOT_API dot_status_t dot_sqr(dot_ctx_t ctx, const uint32_t *a, uint32_t *p, size_t m, size_t batch,
                              dot_stream_t stream)
 {
-    dot_status_t rc = dot_check_ctx(ctx);
+    DeviceScope scope;
+    dot_status_t rc = dot_check_ctx(ctx, scope);
     if (rc != DOT_OK) return rc;
     if (batch == 0 || m == 0) return DOT_OK;
     if (m > DOT_MUL_MAX_LIMBS) return DOT_EUNSUPPORTED;
@@ -219,7 +221,8 @@ DOT_API dot_status_t dot_mul_ragged(dot_ctx_t ctx, const uint32_t *a, const uint
                                     const uint64_t *off, const uint64_t *poff, size_t batch,
                                     dot_stream_t stream)
 {
-    dot_status_t rc = dot_check_ctx(ctx);
+    DeviceScope scope;
+    dot_status_t rc = dot_check_ctx(ctx, scope);
     if (rc != DOT_OK) return rc;
     if (batch == 0) return DOT_OK;
     if (!a || !b || !p || !off || !poff) return DOT_EINVAL;

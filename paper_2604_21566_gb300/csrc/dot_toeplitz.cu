@@ -896,7 +896,8 @@ extern "C" {
 DOT_API dot_status_t dot_mul_shared(dot_ctx_t ctx, const uint32_t *fixed, const uint32_t *b, uint32_t *p,
                                     size_t m, size_t batch, int use_tensor_cores, dot_stream_t stream)
 {
-    dot_status_t rc = dot_check_ctx(ctx);
+    DeviceScope scope;
+    dot_status_t rc = dot_check_ctx(ctx, scope);
     if (rc != DOT_OK) return rc;
     if (batch == 0 || m == 0) return DOT_OK;
     if (!fixed || !b || !p) return DOT_EINVAL;

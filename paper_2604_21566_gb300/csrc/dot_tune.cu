@@ -59,7 +59,8 @@ DOT_API dot_status_t dot_tune_get(dot_ctx_t ctx, int op, size_t m, int *value)
 
 DOT_API dot_status_t dot_autotune(dot_ctx_t ctx, int op, size_t m, size_t batch, int *best, float *best_ms)
 {
-    dot_status_t rc = dot_check_ctx(ctx);
+    DeviceScope scope;
+    dot_status_t rc = dot_check_ctx(ctx, scope);
     if (rc != DOT_OK) return rc;
     if (!best || op < DOT_OP_ADD || op > DOT_OP_MUL || m == 0 || batch == 0) return DOT_EINVAL;
     if (m > SIZE_MAX / 16 / batch) return DOT_EINVAL;
