@@ -426,7 +426,8 @@ def reference_arm(args, rank, world):
 def profile_case(args):
     """Small cases for ncu, a few launches each:
     add  -- dot_add on 2^18 pairs of 4096-bit operands (403 MB, > L2);
-    long -- dot_add on 16 pairs of 2^22-bit operands (25 MB, look-back tiles);
+    long -- dot_add on 64 pairs of 2^22-bit operands (100 MB, look-back tiles:
+            the bench's own part, at the bench's grid);
     mul  -- dot_mul on 2^16 pairs of 8192-bit operands (256 MB in + out);
     shared -- dot_mul_shared on the tensor cores, 2^16 x 2048-bit (50 MB)."""
     import torch
@@ -448,7 +449,7 @@ def profile_case(args):
     if args.case == "mul":
         x, y, _ = W.batched_mul(256)
     elif args.case == "long":
-        x, y = W.addsub_bandwidth(short_batch=0, long_batch=16)["add_long"]
+        x, y = W.addsub_bandwidth(short_batch=0, long_batch=64)["add_long"]
     else:
         x, y = W.addsub_bandwidth(short_batch=1 << 18, long_batch=0)["add_short"]
     a = torch.from_numpy(x.view(np.int32)).cuda()
@@ -693,6 +694,46 @@ def row_c4(ctx, timer, pk, reps=10):
             "roofline": roof, "cpu_baseline": cpu}
 
 
+def row_n4(ctx, timer, pk, reps=10):
+    """Unsaturated radix (27-bit digits, one mad.wide per digit product, no
+    carry chain) against the saturated 32-bit-limb multiply, at equal bit
+    sizes: 2^16 products each."""
+    import oracle
+    from paper_2604_21566_gb300 import dot
+    from paper_2604_21566_gb300 import workloads as W
+    import torch
+    out = {"workload": "2^16 pairs at 4096 and 8192 bits: radix 2^27 digits (dot_mul_unsat) vs "
+                       "radix 2^32 limbs (dot_mul)", "l2": L2_NOTE, "sizes": {}}
+    exact = True
+    madw = pk["madwide_r8"]["per_s"]
+    for bits_total in (4096, 8192):
+        x, y = W.unsaturated_mul(bits_total)
+        nb, n = x.shape
+        a, b = _dv(x), _dv(y)
+        p = torch.empty((nb, 2 * n), dtype=torch.int32, device="cuda")
+        t_unsat, _ = timer.ms(lambda: dot.mul_unsat(a, b, p, ctx=ctx), reps)
+        want, cpu = _cpu(lambda t: oracle.mul_radix(x, y, W.UNSAT_BITS, threads=t), nb, "Gop/s", f"all {nb} rows")
+        ok = bool(np.array_equal(_hs(p), want))
+        exact &= ok
+        xs, ys, _ = W.batched_mul(bits_total // 32)
+        m = xs.shape[1]
+        a2, b2 = _dv(xs), _dv(ys)
+        p2 = torch.empty((nb, 2 * m), dtype=torch.int32, device="cuda")
+        t_sat, _ = timer.ms(lambda: dot.mul(a2, b2, p2, ctx=ctx), reps)
+        rate = nb * n * n / (t_unsat * 1e-3)
+        out["sizes"][f"{bits_total}_bit"] = {
+            "digits": n, "limbs": m, "ms_unsat": round(t_unsat, 4), "ms_saturated": round(t_sat, 4),
+            "unsat_time_vs_saturated": round(t_unsat / t_sat, 3), "bit_exact": ok,
+            "roofline": {"bound": "alu", "achieved": round(rate, 1), "unit": "digit products/s",
+                         "peak": round(madw, 1), "frac": round(rate / madw, 4),
+                         "peak_source": "measured: mad.wide.u32 column-sum probe (libdotprobe)"},
+            "cpu_baseline": cpu}
+        del a, b, p, a2, b2, p2
+    out["bit_exact"] = exact
+    out["bit_exact_rows"] = "all"
+    return out
+
+
 # 128 x 128 x 16 MMA units the Toeplitz kernel issues per tile of 128
 # operands at m = 64: per accumulator half one rank-one bias product at N = 256
 # (2 units) and 8 k-steps at N = 256 (16 units) plus 8 at N = 128 (8 units)
@@ -752,7 +793,8 @@ def workload_rows(ctx, stream, local):
             "C1_correctness_mix": row_c1(ctx, timer, pk),
             "C3_batched_mul": row_c3(ctx, timer, pk),
             "C4_ragged_mixed": row_c4(ctx, timer, pk),
-            "C5_shared_operand": row_c5(ctx, timer, pk)}
+            "C5_shared_operand": row_c5(ctx, timer, pk),
+            "N4_unsaturated_radix": row_n4(ctx, timer, pk)}
     rows["clocks"] = sampler.stop()
     return rows
 
@@ -799,6 +841,8 @@ def suite(args):
         emit("C4_ragged_mixed", row_c4(ctx, timer, pk))
     if want("shared"):
         emit("C5_shared_operand", row_c5(ctx, timer, pk))
+    if want("unsat"):
+        emit("N4_unsaturated_radix", row_n4(ctx, timer, pk))
     if want("mulx"):
         # batched multiply between and above the workload's sizes: one size
         # for each further column shape (12 columns on 16 lanes, 12 on 25, 16)
@@ -856,7 +900,7 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run only the small ncu case of the dominant kernel")
     ap.add_argument("--launches", type=int, default=3)
-    ap.add_argument("--only", default="", help="--suite rows to run: mix,mul,mixed,shared,mulx,sqr,kara")
+    ap.add_argument("--only", default="", help="--suite rows to run: mix,mul,mixed,shared,unsat,mulx,sqr,kara")
     ap.add_argument("--case", choices=["add", "long", "mul", "shared"], default="add",
                     help="which kernel --profile-case runs")
     ap.add_argument("--gpus", type=int, default=1)

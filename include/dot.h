@@ -62,6 +62,9 @@ enum { DOT_OP_ADD = 0, DOT_OP_SUB = 1, DOT_OP_MUL = 2 };
 #define DOT_MUL_MAX_LIMBS 512
 /* Largest operand (limbs) of dot_mul_karatsuba (2^25 bits). */
 #define DOT_KARA_MAX_LIMBS (1u << 20)
+/* Digit width and largest operand (digits) of dot_mul_unsat. */
+#define DOT_UNSAT_BITS 27
+#define DOT_UNSAT_MAX_DIGITS 512
 
 typedef struct dot_ctx *dot_ctx_t;
 typedef void *dot_stream_t;   /* cudaStream_t */
@@ -191,6 +194,20 @@ DOT_API dot_status_t dot_sqr(dot_ctx_t ctx, const uint32_t *a, uint32_t *p, size
  * calls on one ctx must not overlap on the GPU. */
 DOT_API dot_status_t dot_mul_karatsuba(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b,
                                        uint32_t *p, size_t m, size_t batch, dot_stream_t stream);
+
+/* Batched product in an UNSATURATED radix (Sec. 2.1: limbs that keep
+ * headroom to simplify carry handling; the paper's 5x5 multiply uses 52-bit
+ * digits, Sec. 3.3).  An operand of n digits is A = sum_{i<n} A_i 2^(27 i),
+ * each digit a uint32_t below 2^27 (DOT_UNSAT_BITS); p[k] = a[k] * b[k] as
+ * exactly 2n such digits.  a, b: uint32_t[batch][n]; p: uint32_t[batch][2n],
+ * no overlap with the inputs.  Every partial product is one 32 x 32 -> 64-bit
+ * multiply-add into a 64-bit column sum (no carry chain: up to 2^10 digit
+ * products fit), then the carry pass of Alg. 2 Phase 5 in radix 2^27.
+ * 1 <= n <= DOT_UNSAT_MAX_DIGITS, else DOT_EUNSUPPORTED (n == 0: no-op).  An
+ * input digit of 2^27 or more records DOT_EINVAL in the ctx (read by
+ * dot_ctx_check) and leaves that product unspecified. */
+DOT_API dot_status_t dot_mul_unsat(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b, uint32_t *p,
+                                   size_t n, size_t batch, dot_stream_t stream);
 
 /* Ragged product: op k has m_k = off[k+1] - off[k] limbs (<= DOT_MUL_MAX_LIMBS,
  * larger ops record DOT_EUNSUPPORTED in the ctx and are skipped); its 2 m_k

@@ -70,6 +70,8 @@ def bind(path: str):
         f.restype = ctypes.c_int
     L.oracle_sqr.argtypes = [_u32p, _u32p, _sz, _sz]
     L.oracle_sqr.restype = ctypes.c_int
+    L.oracle_mul_radix.argtypes = [_u32p, _u32p, _u32p, _sz, _sz, ctypes.c_uint]
+    L.oracle_mul_radix.restype = ctypes.c_int
     return L
 
 
@@ -175,6 +177,21 @@ def sqr(a):
     B, m = a.shape
     p = np.empty((B, 2 * m), dtype=np.uint32)
     _check(lib().oracle_sqr(_p32(a), _p32(p), m, B), "oracle_sqr")
+    return p
+
+
+def mul_radix(a, b, bits: int, threads: int = 1):
+    """P = A * B for n-digit operands in radix 2^bits (each digit below 2^bits
+    in a 32-bit word), as 2n digits below 2^bits, row by row."""
+    a, b = _batched(a, b)
+    B, n = a.shape
+    p = np.empty((B, 2 * n), dtype=np.uint32)
+    L = lib()
+
+    def fn(x, y, z, n_, rows):
+        return L.oracle_mul_radix(x, y, z, n_, rows, bits)
+    fn.__name__ = "oracle_mul_radix"
+    _run_rows(fn, a, b, p, None, n, B, threads, out_limbs=2 * n)
     return p
 
 

@@ -21,6 +21,9 @@
  *         mb <= ma limbs padded with zeros (as in Theorem 2's proof), and
  *         the borrow mirror D - b X^ma = A - B - bin
  *   sqr : P = A * A as 2m limbs
+ *   mul_radix : P = A * B for operands in an unsaturated radix 2^k, k <= 31
+ *         (Sec. 2.1: each digit kept below 2^k inside a 32-bit word), as 2n
+ *         digits each below 2^k
  * The add/sub loops are the textbook S_i = A_i + B_i + C_{i-1} recurrence
  * (Sec. 2.2 and Alg. 3, MPN-ADD-M) with 64-bit intermediates; the product is
  * the ROW-wise schoolbook (operand scanning), deliberately not the column form
@@ -291,5 +294,34 @@ int oracle_sqr(const uint32_t *a, uint32_t *p, size_t m, size_t batch)
     if (batch && m && (!a || !p)) return -1;
     for (size_t k = 0; k < batch; ++k)
         mul_one(a + k * m, a + k * m, p + 2 * k * m, m);
+    return 0;
+}
+
+/* ---- unsaturated radix: n digits of k bits (k <= 31), each in a 32-bit word.
+ * P = A * B as exactly 2n digits below 2^k, by the row-wise schoolbook in radix
+ * 2^k: t = a_i b_j + p_{i+j} + c < 2^(2k) + 2^(k+1) fits 64 bits.  Returns -1
+ * on a bad argument or an input digit of 2^k or more. */
+int oracle_mul_radix(const uint32_t *a, const uint32_t *b, uint32_t *p, size_t n, size_t batch,
+                     unsigned k)
+{
+    if (k < 1 || k > 31) return -1;
+    if (batch && n && (!a || !b || !p)) return -1;
+    const uint64_t mask = ((uint64_t)1 << k) - 1;
+    for (size_t r = 0; r < batch; ++r) {
+        const uint32_t *x = a + r * n, *y = b + r * n;
+        uint32_t *z = p + 2 * r * n;
+        for (size_t i = 0; i < n; ++i)
+            if (x[i] > mask || y[i] > mask) return -1;
+        for (size_t i = 0; i < 2 * n; ++i) z[i] = 0;
+        for (size_t i = 0; i < n; ++i) {
+            uint64_t c = 0;
+            for (size_t j = 0; j < n; ++j) {
+                const uint64_t t = (uint64_t)x[i] * (uint64_t)y[j] + (uint64_t)z[i + j] + c;
+                z[i + j] = (uint32_t)(t & mask);
+                c = t >> k;
+            }
+            z[i + n] = (uint32_t)c;
+        }
+    }
     return 0;
 }

@@ -22,6 +22,8 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "dot.h")
 OK, EINVAL, ECUDA, ENOMEM, ETIMEOUT, EUNSUPPORTED = range(6)
 OP_ADD, OP_SUB, OP_MUL = 0, 1, 2
 MUL_MAX_LIMBS = 512
+UNSAT_BITS = 27
+UNSAT_MAX_DIGITS = 512
 
 
 class DotUnavailable(ImportError):
@@ -81,6 +83,7 @@ _SIGS = {
     "dot_sub_unequal": (_st, [_vp, _vp, _sz, _vp, _sz, _vp, _vp, _sz, _vp]),
     "dot_sqr": (_st, [_vp, _vp, _vp, _sz, _sz, _vp]),
     "dot_mul_karatsuba": (_st, [_vp, _vp, _vp, _vp, _sz, _sz, _vp]),
+    "dot_mul_unsat": (_st, [_vp, _vp, _vp, _vp, _sz, _sz, _vp]),
     "dot_tune_set": (_st, [_vp, ctypes.c_int, _sz, ctypes.c_int]),
     "dot_tune_get": (_st, [_vp, ctypes.c_int, _sz, ctypes.POINTER(ctypes.c_int)]),
     "dot_autotune": (_st, [_vp, ctypes.c_int, _sz, _sz, ctypes.POINTER(ctypes.c_int),
@@ -357,6 +360,24 @@ def mul_karatsuba(a, b, out=None, ctx=None, stream=None):
     ctx = ctx or default_context(a.device.index)
     _chk(lib().dot_mul_karatsuba(ctx.handle, _ptr(a), _ptr(b), _ptr(out), m, batch, _stream(stream)),
          "dot_mul_karatsuba")
+    return out
+
+
+def mul_unsat(a, b, out=None, ctx=None, stream=None):
+    """p = a * b for n-digit operands in radix 2^27 (each digit below 2^27 in
+    a 32-bit word), as 2n digits below 2^27, row by row."""
+    import torch
+    _limb_tensor(a, "a"), _limb_tensor(b, "b")
+    if a.dim() != 2 or a.shape != b.shape:
+        raise ValueError("dot_mul_unsat: a, b must be [batch, n] of one shape")
+    batch, n = a.shape
+    if out is None:
+        out = torch.empty((batch, 2 * n), dtype=a.dtype, device=a.device)
+    _limb_tensor(out, "out")
+    if tuple(out.shape) != (batch, 2 * n):
+        raise ValueError("dot_mul_unsat: out must be [batch, 2n]")
+    ctx = ctx or default_context(a.device.index)
+    _chk(lib().dot_mul_unsat(ctx.handle, _ptr(a), _ptr(b), _ptr(out), n, batch, _stream(stream)), "dot_mul_unsat")
     return out
 
 

@@ -346,6 +346,52 @@ def ragged_uniform(g: np.random.Generator, sizes, cls: str = "uniform"):
     return a, b, off
 
 
+# unsaturated radix (Sec. 2.1): digits of UNSAT_BITS bits in 32-bit words
+UNSAT_BITS = 27
+SEED_UNSATURATED = 1006
+
+
+def radix_operands(g: np.random.Generator, cls: str, batch: int, n: int, bits: int = UNSAT_BITS):
+    """A pair of operand batches of n digits in radix 2^bits (each digit
+    below 2^bits in a uint32 word), of one class: uniform, max_pair (every
+    digit 2^bits - 1), zeros, sparse (digits nonzero with probability 0.01),
+    ones (x all maximal digits, y with only digit 0 nonzero)."""
+    shape = (batch, n)
+    top = 1 << bits
+    if cls == "uniform":
+        return (g.integers(0, top, size=shape, dtype=np.uint32), g.integers(0, top, size=shape, dtype=np.uint32))
+    if cls == "max_pair":
+        x = np.full(shape, top - 1, dtype=np.uint32)
+        return x, x.copy()
+    if cls == "zeros":
+        return np.zeros(shape, np.uint32), np.zeros(shape, np.uint32)
+    if cls == "sparse":
+        x = np.where(g.random(shape) < 0.01, g.integers(1, top, size=shape, dtype=np.uint32), 0).astype(np.uint32)
+        y = np.where(g.random(shape) < 0.01, g.integers(1, top, size=shape, dtype=np.uint32), 0).astype(np.uint32)
+        return x, y
+    if cls == "ones":
+        x = np.full(shape, top - 1, dtype=np.uint32)
+        y = np.zeros(shape, dtype=np.uint32)
+        if n:
+            y[:, 0] = g.integers(1, top, size=batch, dtype=np.uint32)
+        return x, y
+    raise ValueError(f"unknown class {cls}")
+
+
+def unsaturated_mul(bits_total: int, seed: int = SEED_UNSATURATED, batch: int = 1 << 16,
+                    bits: int = UNSAT_BITS):
+    """2^16 pairs of ceil(bits_total / bits)-digit operands in radix 2^bits:
+    uniform digits, 10% of the pairs both all-maximal digits (largest column
+    sums).  Returns (x, y)."""
+    n = -(-bits_total // bits)
+    g = rng(seed + 7919 * n)
+    x, y = radix_operands(g, "uniform", batch, n, bits)
+    maxed = g.random(batch) < 0.10
+    x[maxed] = (1 << bits) - 1
+    y[maxed] = (1 << bits) - 1
+    return x, y
+
+
 def shared_operand(seed: int = SEED_SHARED_OPERAND, batch: int = 1 << 16, m: int = 64):
     """One fixed uniform m-limb multiplier and ``batch`` uniform m-limb
     operands (default 2048-bit).  Returns (fixed[m], b[batch][m])."""

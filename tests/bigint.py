@@ -24,3 +24,20 @@ def from_int(v: int, m: int) -> np.ndarray:
 def rows_to_ints(a):
     a = np.asarray(a)
     return [to_int(r) for r in a]
+
+
+def to_int_radix(digits, bits: int) -> int:
+    """Value of little-endian digits in radix 2^bits."""
+    v = 0
+    for x in reversed([int(t) for t in np.asarray(digits).ravel()]):
+        v = (v << bits) | x
+    return v
+
+
+def from_int_radix(v: int, n: int, bits: int) -> np.ndarray:
+    out = np.empty(n, dtype=np.uint32)
+    mask = (1 << bits) - 1
+    for i in range(n):
+        out[i] = v & mask
+        v >>= bits
+    return out

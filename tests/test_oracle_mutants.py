@@ -49,6 +49,10 @@ MUTANTS = [
      "const uint64_t bi = i < mb ? (uint64_t)b[i] : 0xFFFFFFFFu;"),
     ("gen_borrow_in_sign", "const uint64_t t = (uint64_t)a[i] - bi - br;",
      "const uint64_t t = (uint64_t)a[i] - bi + br;"),
+    ("radix_mask_width", "const uint64_t mask = ((uint64_t)1 << k) - 1;",
+     "const uint64_t mask = ((uint64_t)1 << (k - 1)) - 1;"),
+    ("radix_drops_top_carry", "            z[i + n] = (uint32_t)c;", "            z[i + n] = 0;"),
+    ("radix_carry_shift", "                c = t >> k;", "                c = t >> 32;"),
     ("sqr_first_row_operand", "mul_one(a + k * m, a + k * m, p + 2 * k * m, m);",
      "mul_one(a + k * m, a, p + 2 * k * m, m);"),
 ]

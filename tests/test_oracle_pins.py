@@ -21,7 +21,7 @@ import numpy as np
 import pytest
 
 import oracle
-from bigint import X, from_int, rows_to_ints, to_int
+from bigint import X, from_int, from_int_radix, rows_to_ints, to_int, to_int_radix
 from paper_2604_21566_gb300 import workloads as W
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -291,10 +291,43 @@ def pin_closed_forms_variants():
         assert p[0] == 1 and not p[1:m].any() and p[m] == 0xFFFFFFFE and (p[m + 1:] == 0xFFFFFFFF).all()
 
 
+def pin_unsaturated_radix():
+    """The radix-2^k product (Sec. 2.1's unsaturated representation) against
+    Python's integers, brute force over edge digits, the closed form
+    (2^(kn) - 1)^2, and a digit of 2^k or more rejected."""
+    g = W.rng(18)
+    for bits in (27, 31, 16):
+        for n in (1, 2, 3, 5, 8, 31, 64, 129):
+            for cls in ("uniform", "max_pair", "zeros", "sparse", "ones"):
+                x, y = W.radix_operands(g, cls, 4, n, bits)
+                p = oracle.mul_radix(x, y, bits)
+                assert p.shape == (4, 2 * n)
+                assert int(p.max()) < (1 << bits)
+                for k in range(4):
+                    assert to_int_radix(p[k], bits) == to_int_radix(x[k], bits) * to_int_radix(y[k], bits), \
+                        (bits, n, cls, k)
+    bits = 27
+    top = (1 << bits) - 1
+    edge = np.array([0, 1, 2, 1 << 26, top - 1, top], dtype=np.uint32)
+    x = np.repeat(edge, edge.size)[:, None]
+    y = np.tile(edge, edge.size)[:, None]
+    p = oracle.mul_radix(x, y, bits)
+    for k in range(x.shape[0]):
+        assert to_int_radix(p[k], bits) == int(x[k, 0]) * int(y[k, 0])
+    for n in (1, 4, 40):
+        ones = np.full((1, n), top, np.uint32)
+        want = from_int_radix(((1 << (bits * n)) - 1) ** 2, 2 * n, bits)
+        assert (oracle.mul_radix(ones, ones, bits)[0] == want).all()
+        assert want[0] == 1 and want[n] == top - 1 and (want[n + 1:] == top).all()
+    bad = np.array([[1 << bits]], np.uint32)
+    with pytest.raises(RuntimeError):
+        oracle.mul_radix(bad, bad, bits)
+
+
 PINS = [pin_python_int_addsub, pin_python_int_mul, pin_python_int_mul_columns,
         pin_brute_force_small, pin_closed_forms, pin_invariants,
         pin_column_worked_example, pin_ragged_and_mixed, pin_carry_probability,
-        pin_python_int_variants, pin_closed_forms_variants]
+        pin_python_int_variants, pin_closed_forms_variants, pin_unsaturated_radix]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
