@@ -429,17 +429,18 @@ def profile_case(args):
     long -- dot_add on 64 pairs of 2^22-bit operands (100 MB, look-back tiles:
             the bench's own part, at the bench's grid);
     mul  -- dot_mul on 2^16 pairs of 8192-bit operands (256 MB in + out);
-    shared -- dot_mul_shared on the tensor cores, 2^16 x 2048-bit (50 MB)."""
+    shared -- dot_mul_shared on the tensor cores, 2^16 x 2048-bit (50 MB);
+    shared128 -- the same at 4096 bits (two K slices, 100 MB)."""
     import torch
     from paper_2604_21566_gb300 import dot
     from paper_2604_21566_gb300 import workloads as W
     torch.cuda.set_device(0)
     ctx = dot.Context(0)
-    if args.case == "shared":
-        f, bb = W.shared_operand()
+    if args.case in ("shared", "shared128"):
+        f, bb = W.shared_operand(m=128 if args.case == "shared128" else 64)
         fd = torch.from_numpy(f.view(np.int32)).cuda()
         b = torch.from_numpy(bb.view(np.int32)).cuda()
-        p = torch.empty((bb.shape[0], 128), dtype=torch.int32, device="cuda")
+        p = torch.empty((bb.shape[0], 2 * bb.shape[1]), dtype=torch.int32, device="cuda")
         for _ in range(args.launches):
             dot.mul_shared(fd, b, p, tensor_cores=True, ctx=ctx)
         torch.cuda.synchronize()
@@ -734,10 +735,18 @@ def row_n4(ctx, timer, pk, reps=10):
     return out
 
 
-# 128 x 128 x 16 MMA units the Toeplitz kernel issues per tile of 128
-# operands at m = 64: per accumulator half one rank-one bias product at N = 256
-# (2 units) and 8 k-steps at N = 256 (16 units) plus 8 at N = 128 (8 units)
-TZ_UNITS_PER_TILE = 2 * (2 + 16 + 8)
+def tz_units_per_tile(m: int) -> int:
+    """128 x 128 x 16 MMA units the Toeplitz kernel issues per tile of 128
+    operands: per 128-column output block, one rank-one bias product per K
+    slice and 8 k-steps for every 128-digit k-block that meets the block (the
+    issuer's own loop).  m = 64: 4 + 48 = 52; m = 128: 16 + 160 = 176."""
+    kb_n = (4 * m + 127) // 128
+    cb_n = (8 * m + 127) // 128
+    slices = 1 if m <= 64 else 2
+    units = slices * cb_n
+    for cb in range(cb_n):
+        units += 8 * (min(kb_n - 1, cb) - max(0, cb - kb_n) + 1)
+    return units
 
 
 def row_c5(ctx, timer, pk, reps=50):
@@ -761,7 +770,7 @@ def row_c5(ctx, timer, pk, reps=50):
     t_tc, med = timer.ms(lambda: dot.mul_shared(fd, b, p, tensor_cores=True, ctx=ctx), reps)
     ok &= bool(np.array_equal(_hs(p), want))
     tiles = (n + 127) // 128
-    issued = 2.0 * 128 * 128 * 16 * TZ_UNITS_PER_TILE * tiles
+    issued = 2.0 * 128 * 128 * 16 * tz_units_per_tile(m) * tiles
     useful = 2.0 * (4 * m) ** 2 * n
     bytes_moved = n * 12 * m + 4 * m
     tflops = issued / (t_tc * 1e-3) / 1e12
@@ -773,13 +782,48 @@ def row_c5(ctx, timer, pk, reps=50):
             "roofline": {"bound": "tensor", "achieved": round(tflops, 1), "peak": tc_peak, "unit": "TFLOP/s",
                          "frac": round(tflops / tc_peak, 4),
                          "peak_source": f"{src} bf16 burst (fp16 runs at the bf16 rate)",
-                         "issued_units_128x128x16_per_tile": TZ_UNITS_PER_TILE,
+                         "issued_units_128x128x16_per_tile": tz_units_per_tile(m),
                          "useful_tflop_s": round(useful / (t_tc * 1e-3) / 1e12, 1),
                          "frac_useful": round(useful / (t_tc * 1e-3) / 1e12 / tc_peak, 4),
                          "achieved_GB_s": round(bytes_moved / (t_tc * 1e-3) / 1e9, 1),
                          "frac_hbm": round(bytes_moved / (t_tc * 1e-3) / 1e9 / hbm, 4)},
             "int32_roofline": _int_roofline(n * m * m, t_int, pk),
             "cpu_baseline": cpu}
+
+
+def row_n3(ctx, timer, pk, reps=20):
+    """Split-K tensor path: one fixed 4096-bit multiplier x 2^16 4096-bit
+    operands (two K slices of 256 digits) vs the INT32 shared-operand path."""
+    import oracle
+    from paper_2604_21566_gb300 import dot
+    from paper_2604_21566_gb300 import workloads as W
+    import torch
+    hbm, tc_peak, src = measured_peaks()
+    f, bb = W.shared_operand(m=128)
+    n, m = bb.shape
+    fa = np.ascontiguousarray(np.broadcast_to(f, bb.shape))
+    fd, b = _dv(f), _dv(bb)
+    p = torch.empty((n, 2 * m), dtype=torch.int32, device="cuda")
+    want, cpu = _cpu(lambda t: oracle.mul(fa, bb, threads=t), n, "Gop/s", f"all {n} rows")
+    t_sh, _ = timer.ms(lambda: dot.mul_shared(fd, b, p, tensor_cores=False, ctx=ctx), reps)
+    ok = bool(np.array_equal(_hs(p), want))
+    t_tc, med = timer.ms(lambda: dot.mul_shared(fd, b, p, tensor_cores=True, ctx=ctx), reps)
+    ok &= bool(np.array_equal(_hs(p), want))
+    tiles = (n + 127) // 128
+    issued = 2.0 * 128 * 128 * 16 * tz_units_per_tile(m) * tiles
+    useful = 2.0 * (4 * m) ** 2 * n
+    tflops = issued / (t_tc * 1e-3) / 1e12
+    return {"workload": "fixed 4096-bit x 2^16 4096-bit (m = 128, two K slices)", "l2": L2_NOTE,
+            "bit_exact": ok, "bit_exact_rows": "all", "ms_tensor": round(t_tc, 4),
+            "ms_tensor_median": round(med, 4), "ms_int32_shared": round(t_sh, 4),
+            "speedup_tensor_vs_int32": round(t_sh / t_tc, 3),
+            "roofline": {"bound": "tensor", "achieved": round(tflops, 1), "peak": tc_peak, "unit": "TFLOP/s",
+                         "frac": round(tflops / tc_peak, 4),
+                         "peak_source": f"{src} bf16 burst (fp16 runs at the bf16 rate)",
+                         "issued_units_128x128x16_per_tile": tz_units_per_tile(m),
+                         "useful_tflop_s": round(useful / (t_tc * 1e-3) / 1e12, 1),
+                         "frac_useful": round(useful / (t_tc * 1e-3) / 1e12 / tc_peak, 4)},
+            "int32_roofline": _int_roofline(n * m * m, t_sh, pk), "cpu_baseline": cpu}
 
 
 def workload_rows(ctx, stream, local):
@@ -794,6 +838,7 @@ def workload_rows(ctx, stream, local):
             "C3_batched_mul": row_c3(ctx, timer, pk),
             "C4_ragged_mixed": row_c4(ctx, timer, pk),
             "C5_shared_operand": row_c5(ctx, timer, pk),
+            "N3_split_k_tensor": row_n3(ctx, timer, pk),
             "N4_unsaturated_radix": row_n4(ctx, timer, pk)}
     rows["clocks"] = sampler.stop()
     return rows
@@ -841,6 +886,8 @@ def suite(args):
         emit("C4_ragged_mixed", row_c4(ctx, timer, pk))
     if want("shared"):
         emit("C5_shared_operand", row_c5(ctx, timer, pk))
+    if want("splitk"):
+        emit("N3_split_k_tensor", row_n3(ctx, timer, pk))
     if want("unsat"):
         emit("N4_unsaturated_radix", row_n4(ctx, timer, pk))
     if want("mulx"):
@@ -900,8 +947,8 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run only the small ncu case of the dominant kernel")
     ap.add_argument("--launches", type=int, default=3)
-    ap.add_argument("--only", default="", help="--suite rows to run: mix,mul,mixed,shared,unsat,mulx,sqr,kara")
-    ap.add_argument("--case", choices=["add", "long", "mul", "shared"], default="add",
+    ap.add_argument("--only", default="", help="--suite rows to run: mix,mul,mixed,shared,splitk,unsat,mulx,sqr,kara")
+    ap.add_argument("--case", choices=["add", "long", "mul", "shared", "shared128"], default="add",
                     help="which kernel --profile-case runs")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)

@@ -223,10 +223,12 @@ DOT_API dot_status_t dot_mul_ragged(dot_ctx_t ctx, const uint32_t *a, const uint
  * matrix; use_tensor_cores != 0 runs it on the tensor cores (tcgen05.mma,
  * fp16 digits -- the batch's shifted by -128, the fixed operand's balanced
  * to [-128, 128] -- with fp32 accumulation, exact because every partial sum
- * stays an integer within 2^22 of the accumulator's start 1.5 * 2^23) and
- * normalises the carries in the epilogue; it needs 1 <= m <= 64 (2048
- * bits), else DOT_EUNSUPPORTED.  use_tensor_cores
- * == 0 runs the INT32 column-sum path of dot_mul (m <= DOT_MUL_MAX_LIMBS). */
+ * over at most 256 batch digits stays an integer within 2^22 of the
+ * accumulator's start 1.5 * 2^23; operands of 65 to 128 limbs split K into two
+ * such slices whose sums are added as integers before the carry pass) and
+ * normalises the carries in the epilogue; it needs 1 <= m <= 128 (4096
+ * bits), else DOT_EUNSUPPORTED.  use_tensor_cores == 0 runs the INT32
+ * column-sum path of dot_mul (m <= DOT_MUL_MAX_LIMBS). */
 DOT_API dot_status_t dot_mul_shared(dot_ctx_t ctx, const uint32_t *fixed, const uint32_t *b,
                                     uint32_t *p, size_t m, size_t batch, int use_tensor_cores,
                                     dot_stream_t stream);

@@ -13,47 +13,58 @@
 //     a_i = d_i + [d_{i-1} >= 128] - 256 [d_i >= 128]  in [-128, 128]
 // (4m + 1 of them; the same value), and every batch digit enters shifted,
 // s_t = beta_t - 128 in [-128, 127].  Then every product is at most 2^14 in
-// magnitude and every raw sum R_c = sum_t s_t a_{c-t} lies in [-2^22, 2^22],
+// magnitude, and a sum over at most 256 batch digits lies in [-2^22, 2^22],
 // so an fp32 accumulator started at M = 1.5 * 2^23 stays in [2^23, 2^24],
-// where fp32 holds every integer exactly, and its bit pattern minus the bits
-// of M is R_c itself -- no float-to-integer conversion.  The true
+// where fp32 holds every integer exactly and its bit pattern is bits(M) plus
+// the sum -- no float-to-integer conversion.  Operands above 64 limbs have
+// more than 256 batch digits: their K dimension is split into slices of two
+// 128-digit k-blocks, each slice accumulated in a region of its own, and the
+// slices' bit patterns are added as integers before the carry pass.  The true
 // column sum is C_c = R_c + 128 W_c with W_c the sum of the a_u over the
-// window u = c - t, t in [0, 4m): a per-column constant.  With v_c the bits
-// of R_c + M, the product is
+// window u = c - t, t in [0, 4m): a per-column constant.  With v_c the sum of
+// the slices' bits for column c, the product is
 //     P = sum_l (sum_q v_{4l+q} 2^(8q)) 2^(32 l) + K  (mod 2^(64 m)),
-// K = sum_l (128 sum_q W_{4l+q} 2^(8q) - bits(M) * 0x01010101) 2^(32 l), one
-// constant per fixed operand, normalised once into 2m 32-bit limbs; every
-// term is then nonnegative and the per-row carry pass is unsigned.
+// K = sum_l (128 sum_q W_{4l+q} 2^(8q) - S bits(M) 0x01010101) 2^(32 l) for S
+// slices: one constant per fixed operand, normalised once into 2m limbs, so
+// every term is nonnegative and the per-row carry pass is unsigned.
 //
-// Kernel layout (one CTA of 17 warps per SM, persistent over tiles of 128
-// operands; K = 256 digits, 512 output columns):
-//   * T is block-Toeplitz in 128 x 128 blocks: block (k-block kb, column
-//     block cb) depends only on d = cb - kb, and only d = 0, 1, 2 are nonzero.
-//     The three distinct blocks (96 KB of fp16) are built once per CTA in
-//     shared memory, stacked along N (rows 128 d + n), K-major with the
-//     128-byte swizzle.
-//   * Each tile's digits are converted to fp16 into two 32 KB k-block
-//     buffers that swap roles every tile, so that the next tile's first
-//     k-block is staged while the tensor core still works on the current
-//     tile's other k-block.
-//   * One issuer thread issues, per 256-column accumulator half, a rank-one
-//     bias product (3072 x 4096 = M, which also resets the half) and the
-//     k-block products (tcgen05.mma, M = 128, K = 16) into four 128-column
-//     fp32 accumulator blocks filling all 512 tensor-memory columns; each
-//     half is committed to an mbarrier.
-//     Where two column blocks take adjacent Toeplitz blocks from the same
-//     k-block, one N = 256 product covers both: the operands are read from
-//     shared memory once for twice the work, which matters because N = 128
-//     products from shared memory nearly saturate its bandwidth.
-//   * Sixteen worker warps (four per tensor-memory lane quadrant) drain each
-//     half (tcgen05.ld) and release it, build limb values with 64-bit
-//     multiply-adds, carry them serially inside 16-limb segments, exchange
-//     one word per segment to resolve carries across segments, and stage the
-//     half tile in shared memory, while the tensor core fills the other half
-//     and the next tile's limbs are in flight.
-//   * One store thread writes each staged half tile out with two tensor
-//     stores (TMA), off the workers' path; before its first store its warp
-//     computes the constant K while the first tile's products run.
+// Operands of the Toeplitz product.  Reversing the order of the N rows of
+// the B operand of one product turns its Toeplitz block into a Hankel block:
+// row n' holds a_{C - n' - k} for k = 0..127, a window that starts one digit
+// later in a reversed digit array for each next row.  So every block of every
+// diagonal is read from ONE small array: eight interleaved copies of the
+// reversed digits, shifted by 0..7, laid out so that the 16-byte chunk that
+// starts at any index i sits at (i / 8) * 128 + (i % 8) * 16 bytes.  A
+// K-major operand without swizzle then has its 8-row core matrices at 128-byte
+// steps both along N and along K (the two descriptor strides alias, which is
+// fine for an operand that is only read), and the diagonal d = cb - kb only
+// moves the start address.  The product's columns come out reversed inside
+// each 128-column block, which the epilogue undoes when it reads them.
+//
+// Kernel layout (one CTA of 18 warps per SM, persistent over tiles of 128
+// operands; output in blocks of 128 columns = 32 limbs):
+//   * Block pipeline: block i of the CTA's sequence (tile-major) accumulates
+//     in tensor-memory unit i mod (4 / S) (S regions of 128 columns; 512
+//     columns in all), and is drained, regrouped and stored by worker group
+//     i mod 4 (four warps, one per tensor-memory lane quadrant, so that each
+//     thread owns one operand row of the block).  The four groups work on
+//     four consecutive blocks at once; the carry word of each row passes from
+//     block to block through shared memory, and only its addition waits for
+//     the previous block.
+//   * One issuer thread issues, per block and region, a rank-one bias product
+//     (3072 x 4096 = M, which also resets the region) and the products of
+//     every k-block that meets the block (tcgen05.mma, M = 128, N = 128,
+//     K = 16), then commits the block to its unit's mbarrier.
+//   * Batch digits are converted to fp16 in k-block slots of 32 KB: up to 64
+//     limbs two slots per tile, alternating between two pairs from tile to
+//     tile; up to 128 limbs one slot per k-block, each refilled with the next
+//     tile's k-block as soon as the last block that reads it is done.  The
+//     group that finished that block converts, so that conversion runs while
+//     the tensor core works on later blocks.
+//   * Each group stages its block's 32 limbs per row (128-byte swizzle) and
+//     one of its threads writes the block with a tensor store (TMA): one
+//     16 KB box, where per-thread row stores (rows 8m bytes apart) would
+//     split every warp store into 32 partial lines.
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <string.h>
@@ -62,41 +73,40 @@
 #include "dot_plan.h"
 #include "dot_mul.cuh"
 
-#define TZ_WORKERS 512          // 16 worker warps: staging and epilogue
-#define TZ_THREADS (TZ_WORKERS + 64)   // + one issuer warp + one store warp
-#define TZ_M 128                 // operands per tile (MMA M)
-#define TZ_K 256                 // digits per operand (bytes of 64 limbs)
-#define TZ_NB 128                // columns per accumulator block (MMA N)
-#define TZ_MAX_LIMBS 64
-#define TZ_DIGITS (TZ_K + 8)     // balanced digits of the fixed operand (4m + 1 used)
-#define TZ_TBLOCK (128 * 128 * 2)            // bytes of one 128 x 128 fp16 block
-#define TZ_ATILE (TZ_M * TZ_K * 2)           // bytes of the two fp16 k-block buffers
-#define TZ_KBUF (TZ_ATILE / 2)               // one 128-row x 128-digit k-block buffer
-#define TZ_BIAS_A (128 * 16 * 2)             // bias operands, 128 x 16 and 256 x 16 fp16
-#define TZ_BIAS_B (256 * 16 * 2)
-#define TZ_BOX (TZ_M * 128)                // one staged box: 128 rows x 32 limbs, 128-byte swizzle
-#define TZ_OUT (2 * TZ_BOX)                // bytes of one staged half tile of product limbs
-#define TZ_RDIG 512                        // fp16 reversed-digit copy length
-#define TZ_RCOPY (TZ_RDIG * 2 + 16)        // bytes between the 8 shifted copies (padded)
+#define TZ_WORKERS 512                 // 16 worker warps: four groups of four
+#define TZ_THREADS (TZ_WORKERS + 64)   // + the issuer warp + the constant warp
+#define TZ_M 128                       // operands per tile (MMA M)
+#define TZ_MAX_LIMBS 128
+#define TZ_KBUF (TZ_M * 128 * 2)       // one k-block slot: 128 rows x 128 digits, fp16
+#define TZ_SLOTS 4
+#define TZ_DMAX 4                      // most diagonals (k-blocks) that meet one column block
+#define TZ_HLEN (128 * TZ_DMAX + 256)  // entries of the reversed digit array
+#define TZ_HBYTES (TZ_HLEN * 16)       // its eight interleaved copies
+#define TZ_BIAS_BYTES (128 * 16 * 2)   // one bias operand, 128 x 16 fp16
+#define TZ_DIGITS (4 * TZ_MAX_LIMBS + 1)
 // shared-memory carve-up, from a 1024-byte aligned base
-#define TZ_OFF_A (3 * TZ_TBLOCK)
-#define TZ_OFF_OUT (TZ_OFF_A + TZ_ATILE)
-#define TZ_OFF_BIAS (TZ_OFF_OUT + TZ_OUT)                 // bias operands A, B
-#define TZ_OFF_KN (TZ_OFF_BIAS + TZ_BIAS_A + TZ_BIAS_B)   // uint32 [128]: K as normalised limbs
-#define TZ_OFF_XCH (TZ_OFF_KN + 128 * 4)                  // uint2 [2 halves][4 segments][128 rows]
-#define TZ_OFF_CARRY (TZ_OFF_XCH + 2 * 4 * TZ_M * 8)      // int32 [128]: carry word half 0 -> half 1
-#define TZ_OFF_DIG (TZ_OFF_CARRY + TZ_M * 4)              // int32 [TZ_DIGITS]: balanced digits
-#define TZ_OFF_PRE (TZ_OFF_DIG + TZ_DIGITS * 4)           // int32 [TZ_DIGITS + 8]: their prefix sums
-#define TZ_OFF_BARS (TZ_OFF_PRE + (TZ_DIGITS + 8) * 4)    // 10 mbarriers, tensor-memory address, flag
-#define TZ_SMEM (1024 + TZ_OFF_BARS + 128)                // + alignment slack
+#define TZ_BOX (TZ_M * 128)            // one staged block: 128 rows x 32 limbs, 128-byte swizzle
+#define TZ_OFF_A 0
+#define TZ_OFF_OUT (TZ_SLOTS * TZ_KBUF)                   // four staging boxes, one per group
+#define TZ_OFF_H (TZ_OFF_OUT + 4 * TZ_BOX)                // interleaved reversed digits
+#define TZ_OFF_BIAS (TZ_OFF_H + TZ_HBYTES)                // bias operands A, B
+#define TZ_OFF_KN (TZ_OFF_BIAS + 2 * TZ_BIAS_BYTES)       // uint32 [2 * TZ_MAX_LIMBS]: K
+#define TZ_OFF_CW (TZ_OFF_KN + 2 * TZ_MAX_LIMBS * 4)      // uint32 [4][128]: carry words
+#define TZ_DIG_WORDS 576                                  // >= TZ_DIGITS + 40, a multiple of 16 words
+#define TZ_OFF_DIG (TZ_OFF_CW + 4 * TZ_M * 4)             // int32 [TZ_DIG_WORDS]: balanced digits
+#define TZ_OFF_PRE (TZ_OFF_DIG + 4 * TZ_DIG_WORDS)         // int32 [TZ_DIG_WORDS]: their prefix sums
+#define TZ_OFF_BARS (TZ_OFF_PRE + 4 * TZ_DIG_WORDS)        // mbarriers, tensor-memory address, flags
+#define TZ_SMEM (1024 + TZ_OFF_BARS + 256)
+static_assert(TZ_DIG_WORDS >= TZ_DIGITS + 40 && TZ_DIG_WORDS % 16 == 0, "digit arrays");
+static_assert(TZ_OFF_H % 128 == 0 && TZ_OFF_BIAS % 128 == 0 && TZ_OFF_KN % 16 == 0 && TZ_OFF_CW % 16 == 0,
+              "operand and vector alignment");
+static_assert(TZ_OFF_BARS % 16 == 0, "mbarriers are 8-byte aligned");
+static_assert(TZ_OFF_OUT % 1024 == 0 && TZ_BOX % 1024 == 0, "swizzled staging boxes");
+static_assert(TZ_SMEM <= 227 * 1024, "shared memory");
 // fp32 bits of the accumulator start value M = 1.5 * 2^23 = 3072 * 4096
 #define TZ_MAGIC_BITS 0x4B400000u
-#define TZ_TROWS 384             // stacked Toeplitz rows (3 blocks)
 static_assert(TZ_DIGITS <= TZ_THREADS, "one balanced digit per thread");
-// Toeplitz chunk (d, n, k chunk) holds digits a[s0], a[s0-1], .., a[s0-7],
-// s0 = 128 d + n - 8 kc in [-120, 383]; with r[i] = a[383 - i] that run is
-// r[383 - s0 .. + 7], which the shifted copy (383 - s0) % 8 holds 16-byte aligned
-#define TZ_RTOP 383
+static_assert(TZ_SMEM <= 227 * 1024, "shared memory");
 
 // ------------------------------------------------------------ tcgen05 glue
 // Shared-memory matrix descriptor, K-major with the 128-byte swizzle: a tile
@@ -183,6 +193,29 @@ __device__ __forceinline__ void tz_ld_wait(uint32_t (&r)[32])
                  :: "memory");
 }
 
+// 16 consecutive columns of this warp's 32 lanes (valid after a wait)
+__device__ __forceinline__ void tz_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                   "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+}
+
+// wait for this thread's tensor-memory loads, pinning two 16-column results
+__device__ __forceinline__ void tz_ld_wait16x2(uint32_t (&a)[16], uint32_t (&b)[16])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]),
+                   "+r"(a[7]), "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]), "+r"(a[12]), "+r"(a[13]),
+                   "+r"(a[14]), "+r"(a[15]), "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]),
+                   "+r"(b[5]), "+r"(b[6]), "+r"(b[7]), "+r"(b[8]), "+r"(b[9]), "+r"(b[10]), "+r"(b[11]),
+                   "+r"(b[12]), "+r"(b[13]), "+r"(b[14]), "+r"(b[15])
+                 :: "memory");
+}
+
 __device__ __forceinline__ void tz_pin(uint32_t (&r)[32])
 {
     asm volatile(""
@@ -243,73 +276,16 @@ __device__ __forceinline__ uint32_t tz_shifted2(uint32_t x, uint32_t sel)
 }
 
 // --------------------------------------------------------------- kernel
-// Staging split in two: the next tile's limbs are loaded into registers early
-// (their latency hides behind the current tile's drain) and converted into the
-// fp16 k-block buffers once the tensor core is done with them.  Worker w holds
-// row w % 128's limbs 8q .. 8q + 7 of each k-block (q = w / 128), so that all
-// workers convert each k-block together: x[0..8) for k-block 0, x[8..16) for 1.
-__device__ __forceinline__ void tz_load(uint32_t (&x)[16], const uint32_t *b, int m, size_t batch, size_t tile, int w)
+// Descriptor of the interleaved reversed-digit array as a K-major operand
+// without swizzle: 8-row core matrices 128 bytes apart both along N (stride
+// offset) and along K (leading offset).
+__device__ __forceinline__ uint64_t tz_desc_hankel(uint32_t saddr)
 {
-    const int row = w & (TZ_M - 1), q = w >> 7;
-    const size_t op = tile * TZ_M + row;
-    const uint32_t *src = b + op * (size_t)m + 8 * q;
-    if (op < batch && m == TZ_MAX_LIMBS && aligned16(src)) {
-#pragma unroll
-        for (int kb = 0; kb < 2; ++kb)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(src + 32 * kb) + h);
-                x[8 * kb + 4 * h] = v.x; x[8 * kb + 4 * h + 1] = v.y;
-                x[8 * kb + 4 * h + 2] = v.z; x[8 * kb + 4 * h + 3] = v.w;
-            }
-    } else {
-#pragma unroll
-        for (int l = 0; l < 16; ++l) {
-            const int limb = 32 * (l >> 3) + 8 * q + (l & 7);
-            x[l] = (op < batch && limb < m) ? __ldcs(b + op * (size_t)m + limb) : 0u;
-        }
-    }
-}
-
-// Digits beyond the operand's 4m enter as 0 (not -128), so that every batch
-// row has exactly the digit window that the limb constants assume.  Worker w
-// converts row w % 128's limbs 8q .. 8q + 7 of k-block kb (q = w / 128):
-// digits 32q .. 32q + 31 of the k-block, into its buffer kbuf.
-__device__ __forceinline__ void tz_convert(unsigned char *kbuf, const uint32_t (&x)[16], int kb, int w, int m)
-{
-    const int row = w & (TZ_M - 1), q = w >> 7;
-    const int limb0 = 32 * kb + 8 * q;   // first limb of the operand held here
-    const bool full = limb0 + 8 <= m;
-#pragma unroll
-    for (int l2 = 0; l2 < 4; ++l2) {
-        const uint32_t x0 = x[8 * kb + 2 * l2], x1 = x[8 * kb + 2 * l2 + 1];
-        uint4 v = make_uint4(tz_shifted2(x0, 0x4140), tz_shifted2(x0, 0x4342), tz_shifted2(x1, 0x4140),
-                             tz_shifted2(x1, 0x4342));
-        if (!full) {
-            if (limb0 + 2 * l2 >= m) v.x = v.y = 0u;
-            if (limb0 + 2 * l2 + 1 >= m) v.z = v.w = 0u;
-        }
-        *reinterpret_cast<uint4 *>(kbuf + tz_off(row, 32 * q + 8 * l2, TZ_M)) = v;
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// k-block kb of tile number it (counted per CTA) lives in buffer kb ^ (it & 1)
-__device__ __forceinline__ unsigned char *tz_kbuf(unsigned char *sA, int kb, int it)
-{
-    return sA + TZ_KBUF * (kb ^ (it & 1));
-}
-
-__device__ __forceinline__ void tz_workers_sync() { asm volatile("bar.sync 1, %0;" :: "n"(TZ_WORKERS) : "memory"); }
-
-// worker barrier that also returns whether any worker passed v != 0
-__device__ __forceinline__ int tz_workers_sync_or(int v)
-{
-    int r;
-    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\t"
-                 "bar.red.or.pred q, 1, %2, p;\n\tselp.s32 %0, 1, 0, q;\n\t}"
-                 : "=r"(r) : "r"(v), "n"(TZ_WORKERS) : "memory");
-    return r;
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)(128 >> 4) << 16;   // next 8-k chunk
+    d |= (uint64_t)(128 >> 4) << 32;   // next 8 rows
+    d |= (uint64_t)1 << 46;
+    return d;
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
@@ -317,7 +293,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(bar)) : "memory");
 }
 
-// One arrival per warp once all its lanes got here (worker barriers count
+// One arrival per warp once all its lanes got here (barrier counts are in
 // warps: hundreds of single-thread arrivals on one barrier word serialise).
 __device__ __forceinline__ void tz_warp_arrive(uint64_t *bar)
 {
@@ -325,197 +301,79 @@ __device__ __forceinline__ void tz_warp_arrive(uint64_t *bar)
     if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
 }
 
-// k-steps of one product: a k-block buffer (descriptor adesc of its base)
-// against stacked Toeplitz rows from 128 d0 (descriptor bdesc of that row),
-// n = 128 or 256 of them, into accumulator columns col; the first step
-// overwrites the accumulator when acc0 == 0.  Unrolled with constant
-// descriptor offsets (the start-address field holds address / 16): the
-// issuing warp shares its scheduler with busy worker warps, so each product
-// must cost it only a few independent instructions.
-__device__ __forceinline__ void tz_issue_kblock(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                                uint32_t acc0)
+// Barrier 2 + g among the four warps of worker group g, which also returns
+// whether any of them passed v != 0.
+__device__ __forceinline__ int tz_group_sync_or(int g, int v)
 {
+    int r;
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\t"
+                 "bar.red.or.pred q, %2, 128, p;\n\tselp.s32 %0, 1, 0, q;\n\t}"
+                 : "=r"(r) : "r"(v), "r"(2 + g) : "memory");
+    return r;
+}
+
+// Conversion unit (k-block kb, row half rh) of a tile: 64 rows x 32 limbs,
+// 16 limbs per thread of a worker group (thread j: row 64 rh + j / 2, limbs
+// 16 (j % 2) .. + 15 of the k-block).  Rows past the batch read as zero.
+__device__ __forceinline__ void tz_unit_load(uint32_t (&x)[16], const uint32_t *b, int m, size_t batch, size_t tile,
+                                             int kb, int rh, int j)
+{
+    const int row = 64 * rh + (j >> 1);
+    const size_t op = tile * TZ_M + row;
+    const int l0 = 32 * kb + 16 * (j & 1);
+    const uint32_t *src = b + op * (size_t)m + l0;
+    // volatile: the loads issue here, not next to their first use, so that
+    // their latency overlaps the work in between
+    if (op < batch && l0 + 16 <= m && aligned16(src)) {
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
-        // k = 16 s inside the k-block: atom column s / 4, 32 bytes per step inside it
-        const uint64_t ad = adesc + (uint64_t)(((s >> 2) * TZ_M * 128 + (s & 3) * 32) >> 4);
-        const uint64_t bd = bdesc + (uint64_t)(((s >> 2) * TZ_TROWS * 128 + (s & 3) * 32) >> 4);
-        tz_mma(dtmem, ad, bd, idesc, s > 0 ? 1u : acc0);
+        for (int h = 0; h < 4; ++h)
+            asm volatile("ld.global.cs.v4.u32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(x[4 * h]), "=r"(x[4 * h + 1]), "=r"(x[4 * h + 2]), "=r"(x[4 * h + 3])
+                         : "l"(src + 4 * h));
+    } else {
+#pragma unroll
+        for (int l = 0; l < 16; ++l) {
+            x[l] = 0u;
+            if (op < batch && l0 + l < m) asm volatile("ld.global.cs.u32 %0, [%1];" : "=r"(x[l]) : "l"(src + l));
+        }
     }
 }
 
-// Epilogue of accumulator half h for operand row `row`, limbs [64 h + 16 seg,
-// + 16); mid(late) runs between the arithmetic and the exchange.  Limb position l collects sum_q v_{4l+q} 2^(8q) + K_l (unsigned,
-// below 2^56); a serial carry inside the segment gives 16 limbs and a carry
-// word.  Each segment publishes (carry word, first limb, "limbs 1..15 all
-// ones"), from which every segment derives its incoming carry word: adding a
-// word w to a segment whose first limb is o_0 moves a carry out of it only if
-// o_0 + w >= 2^32 and the rest are all ones.  carry_h holds, per row, the
-// carry word from half 0 into half 1; the carry out of the top limb is
-// dropped (the product is taken mod 2^(64 m), which it fits).
-template <typename Mid>
-__device__ __forceinline__ int tz_epilogue(Mid mid, uint32_t tmem, int h, int quad, int seg, int lane, uint64_t *bar_free,
-                                           const uint32_t *Kn, uint2 *xch, uint32_t *carry_h, uint32_t *out,
-                                           uint32_t *p, int m, size_t batch, size_t tile, int late,
-                                           const CUtensorMap *pmap, uint64_t *bar_staged_out, uint64_t *bar_out_free,
-                                           int use, uint32_t *out_flags, int &late_out, uint32_t *status,
-                                           uint64_t wait_ns)
+// The unit's digits, shifted by -128, as fp16 into a k-block slot (128-byte
+// swizzled, K-major).  Digits beyond the operand's 4m enter as 0 (not -128),
+// so that every batch row has exactly the digit window the constant K assumes.
+__device__ __forceinline__ void tz_unit_convert(unsigned char *slot, const uint32_t (&x)[16], int kb, int rh, int j,
+                                                int m)
 {
-    const int row = 32 * quad + lane;
-    const int w = 32 * (4 * seg + quad) + lane;   // worker index
-    const uint32_t taddr = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(256 * h + 64 * seg);
-    const uint4 *kq = reinterpret_cast<const uint4 *>(Kn + 64 * h + 16 * seg);
-    uint32_t o[16];
-    uint32_t hi = 0;
-    // two passes of 32 columns (8 limbs) keep register pressure down
+    const int row = 64 * rh + (j >> 1);
+    const int lk0 = 16 * (j & 1);
+    const int limb0 = 32 * kb + lk0;
 #pragma unroll
-    for (int pass = 0; pass < 2; ++pass) {
-        uint32_t v[32];
-        tz_ld32(taddr + 32 * pass, v);
-        tz_ld_wait(v);
-        if (pass == 1) {
-            // all of this thread's columns are in registers: the tensor core may refill them
-            tz_fence_before();
-            tz_warp_arrive(bar_free);
-        }
-        // the limb values first (independent of each other), then the carry
-        // chain, which costs two dependent adds per limb
-        uint64_t L[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int l = 8 * pass + j;
-            const uint4 k4 = kq[l >> 2];
-            const uint32_t k = (l & 3) == 0 ? k4.x : (l & 3) == 1 ? k4.y : (l & 3) == 2 ? k4.z : k4.w;
-            L[j] = (uint64_t)k + v[4 * j] + (uint64_t)v[4 * j + 1] * 256u + (uint64_t)v[4 * j + 2] * 65536u +
-                   (uint64_t)v[4 * j + 3] * 16777216u;
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const uint64_t acc = L[j] + hi;
-            o[8 * pass + j] = (uint32_t)acc;
-            hi = (uint32_t)(acc >> 32);
-        }
+    for (int l2 = 0; l2 < 8; ++l2) {
+        const uint32_t x0 = x[2 * l2], x1 = x[2 * l2 + 1];
+        uint4 v = make_uint4(tz_shifted2(x0, 0x4140), tz_shifted2(x0, 0x4342), tz_shifted2(x1, 0x4140),
+                             tz_shifted2(x1, 0x4342));
+        if (limb0 + 2 * l2 >= m) v.x = v.y = 0u;
+        if (limb0 + 2 * l2 + 1 >= m) v.z = v.w = 0u;
+        *reinterpret_cast<uint4 *>(slot + tz_off(row, 4 * (lk0 + 2 * l2), TZ_M)) = v;
     }
-    uint32_t all1 = o[1];
-#pragma unroll
-    for (int l = 2; l < 16; ++l) all1 &= o[l];
-    if (seg < 3) xch[seg * TZ_M + row] = make_uint2((hi << 1) | (uint32_t)(all1 == DOT_FULL), o[0]);
-    // work that should not wait for the rest of the epilogue (it may change late)
-    mid(late);
-    // every worker learns whether any of them found its products late
-    const int any_late = tz_workers_sync_or(late);
-    uint32_t c = h ? carry_h[row] : 0u;
-    for (int q = 0; q < seg; ++q) {
-        const uint2 e = xch[q * TZ_M + row];
-        const uint64_t s0 = (uint64_t)e.y + c;
-        c = (e.x >> 1) + (uint32_t)((s0 >> 32) != 0 && (e.x & 1u));
-    }
-    // add the incoming carry word; a carry out of the first limb ripples
-    // through the rest only while they are all ones
-    const uint64_t s0 = (uint64_t)o[0] + c;
-    o[0] = (uint32_t)s0;
-    uint32_t rip = (uint32_t)(s0 >> 32);   // 0 or 1
-    if (rip != 0) {
-#pragma unroll
-        for (int l = 1; l < 16; ++l) {
-            const uint32_t x = o[l];
-            o[l] = x + rip;
-            rip = x == DOT_FULL ? rip : 0u;
-        }
-    }
-    if (h == 0 && seg == 3) carry_h[row] = hi + rip;
-    // stage this segment's 16 result limbs once the store thread has read the
-    // previous half tile out of the staging buffer (a wait that runs out is
-    // recorded, the half tile is not stored, and the next vote stops the CTA)
-    late_out = use > 0 && !mbar_wait_bounded(bar_out_free, (uint32_t)((use - 1) & 1), wait_ns);
-    if (late_out) {
-        record_status(status, DOT_ETIMEOUT);
-        atomicOr(out_flags, 1u);   // skip this half tile's stores
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-        *reinterpret_cast<uint4 *>(tz_stage(out, row, 4 * seg + q)) =
-            make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
-    if (w == 0 && any_late) atomicOr(out_flags, 3u);   // skip, and stop after this tile
-    if (pmap) {
-        // the store thread writes the half tile out
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        tz_warp_arrive(bar_staged_out);
-        return any_late;
-    }
-    const int skip = tz_workers_sync_or(late_out) | any_late;
-    if (!skip) {
-        const int l0 = 64 * h;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int g = w + TZ_WORKERS * k, orw = g >> 4, cc = g & 15;   // 16 chunks of 4 limbs per row
-            const size_t op = tile * TZ_M + orw;
-            const int lc = l0 + 4 * cc;
-            if (op < batch && lc < 2 * m) {
-                const uint4 vv = *reinterpret_cast<const uint4 *>(tz_stage(out, orw, cc));
-                uint32_t *dst = p + op * (size_t)(2 * m) + lc;
-                const uint32_t e4[4] = {vv.x, vv.y, vv.z, vv.w};
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (lc + e < 2 * m) st_stream1(dst + e, e4[e]);
-            }
-        }
-    }
-    // the staging buffer is free again once every worker has read its chunks
-    tz_warp_arrive(bar_staged_out);
-    return any_late;
-}
-
-// The store thread: per staged half tile, two tensor stores (limbs 64 h + 0..31,
-// + 32..63 of the tile's 128 rows; rows past the batch and limbs past 2m are
-// clipped), then the staging buffer is handed back once the stores have read
-// it.  Without a tensor map the workers store, and this thread only passes the
-// buffer on.  It mirrors the workers' tile loop and stops where they stop.
-__device__ __forceinline__ void tz_store_loop(const CUtensorMap *pmap, const uint32_t *out, uint64_t *bar_staged_out,
-                                              uint64_t *bar_out_free, volatile uint32_t *out_flags, int m,
-                                              size_t ntiles, uint64_t wait_ns)
-{
-    if (pmap) asm volatile("prefetch.tensormap [%0];" :: "l"(pmap) : "memory");
-    int use = 0;
-    uint32_t stop = 0;
-    for (size_t tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x) {
-        for (int h = 0; h < 2; ++h, ++use) {
-            if (!mbar_wait_bounded(bar_staged_out, (uint32_t)(use & 1), wait_ns)) {
-                stop = 1;
-                break;
-            }
-            const uint32_t f = *out_flags;
-            *out_flags = 0u;
-            stop |= f & 2u;
-            if (pmap) {
-                const int l0 = 64 * h;
-                if (!(f & 1u)) {
-                    if (l0 < 2 * m) tz_tma_store(pmap, out, l0, (int)(tile * TZ_M));
-                    if (l0 + 32 < 2 * m) tz_tma_store(pmap, out + TZ_BOX / 4, l0 + 32, (int)(tile * TZ_M));
-                }
-                tz_bulk_wait_read();
-            }
-            mbar_arrive(bar_out_free);
-        }
-    }
-    if (pmap) tz_bulk_wait_all();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // The constant K (one warp): prefix sums of the balanced digits, the per-limb
-// constants c_l = 128 sum_q W_{4l+q} 2^(8q) - bits(M) * 0x01010101 (W_c = sum
+// constants c_l = 128 sum_q W_{4l+q} 2^(8q) - S bits(M) 0x01010101 (W_c = sum
 // of a_u over u in [max(0, c - 4m + 1), min(c, 4m)]), and K = sum_{l < 2m}
-// c_l 2^(32 l) as 128 limbs mod 2^(64 m): lane j takes limbs 4j..4j+3 through
-// a signed serial carry, then the lanes pass carry words up until they no
-// longer change.
-__device__ __forceinline__ void tz_make_k(const int32_t *dig, int32_t *pre, uint32_t *Kn, int m, int lane)
+// c_l 2^(32 l) as 2m limbs mod 2^(64 m): each lane takes ceil(2m / 32)
+// consecutive limbs through a signed serial carry, then the lanes pass carry
+// words up until they no longer change.  Limbs from 2m on are 0.
+__device__ __forceinline__ void tz_make_k(const int32_t *dig, int32_t *pre, uint32_t *Kn, int m, int S, int lane)
 {
     const int nd = 4 * m;
-    // prefix sums pre[u] = a_0 + ... + a_{u-1}, 9 digits per lane
-    int loc[9], sum = 0;
+    int loc[17], sum = 0;
 #pragma unroll
-    for (int j = 0; j < 9; ++j) {
-        const int u = 9 * lane + j;
-        loc[j] = u < TZ_DIGITS ? dig[u] : 0;
+    for (int j = 0; j < 17; ++j) {
+        const int u = 17 * lane + j;
+        loc[j] = u <= nd ? dig[u] : 0;
         sum += loc[j];
     }
     int incl = sum;
@@ -526,20 +384,23 @@ __device__ __forceinline__ void tz_make_k(const int32_t *dig, int32_t *pre, uint
     }
     int run = incl - sum;
 #pragma unroll
-    for (int j = 0; j < 9; ++j) {
-        const int u = 9 * lane + j;
-        if (u <= TZ_DIGITS) pre[u] = run;
+    for (int j = 0; j < 17; ++j) {
+        const int u = 17 * lane + j;
+        if (u <= nd + 1) pre[u] = run;
         run += loc[j];
     }
     __syncwarp();
-    uint32_t t[4];
+    // lane j takes limbs lpl j .. lpl j + lpl - 1, lpl = ceil(2m / 32) <= 8
+    const int lpl = (2 * m + 31) >> 5;
+    uint32_t t[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
     int64_t acc = 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int l = 4 * lane + j;
+    for (int j = 0; j < 8; ++j) {
+        if (j >= lpl) break;   // the lane's carry word stays in acc
+        const int l = lpl * lane + j;
         int64_t k = 0;
         if (l < 2 * m) {
-            k = -(int64_t)TZ_MAGIC_BITS * 0x01010101;
+            k = -(int64_t)S * (int64_t)TZ_MAGIC_BITS * 0x01010101;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int c = 4 * l + q;
@@ -552,7 +413,15 @@ __device__ __forceinline__ void tz_make_k(const int32_t *dig, int32_t *pre, uint
         t[j] = (uint32_t)acc;
     }
     const int64_t cw = acc >> 32;   // this lane's carry word with carry-in 0
-    const bool ones = (t[1] & t[2] & t[3]) == DOT_FULL, zeros = (t[1] | t[2] | t[3]) == 0u;
+    uint32_t all = DOT_FULL, any = 0u;
+#pragma unroll
+    for (int j = 1; j < 8; ++j) {
+        if (j < lpl) {
+            all &= t[j];
+            any |= t[j];
+        }
+    }
+    const bool ones = all == DOT_FULL, zeros = any == 0u;
     int64_t ci = __shfl_up_sync(0xffffffffu, cw, 1);
     if (lane == 0) ci = 0;
     for (int round = 0; round < 32; ++round) {
@@ -563,131 +432,139 @@ __device__ __forceinline__ void tz_make_k(const int32_t *dig, int32_t *pre, uint
         if (__all_sync(0xffffffffu, nci == ci)) break;
         ci = nci;
     }
-    // apply the carry-in word: a carry or borrow out of limb 0 ripples
-    // while the next limbs are all ones / all zero
+    // apply the carry-in word: a carry or borrow out of limb 0 ripples while
+    // the next limbs are all ones / all zero
     const int64_t s0 = (int64_t)t[0] + ci;
     t[0] = (uint32_t)s0;
     int32_t rip = (int32_t)(s0 >> 32);
 #pragma unroll
-    for (int j = 1; j < 4; ++j) {
+    for (int j = 1; j < 8; ++j) {
         const uint32_t x = t[j];
         t[j] = x + (uint32_t)rip;
         rip = (rip > 0 && x == DOT_FULL) || (rip < 0 && x == 0u) ? rip : 0;
     }
-    reinterpret_cast<uint4 *>(Kn)[lane] = make_uint4(t[0], t[1], t[2], t[3]);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int l = lpl * lane + j;
+        if (j < lpl && l < 2 * m) Kn[l] = t[j];
+    }
+    // limbs past 2m (the rest of the top column block) are 0
+    for (int l = 2 * m + lane; l < 2 * TZ_MAX_LIMBS; l += 32) Kn[l] = 0u;
 }
 
-// fixed: m limbs (m <= 64), b: [batch][m], p: [batch][2m].
-// Warp specialised: warp 16 allocates tensor memory and issues every product
-// (one lane); warps 0..15 stage operand tiles as fp16 digits and drain the
-// accumulators.  The 512 accumulator columns are two halves (column blocks
-// 0-1 and 2-3) so that the tensor core fills one half while the workers drain
-// the other:
-//   issuer : for each tile t: wait staged(t); wait free0(t-1); issue half 0
-//            -> full0(t); wait free1(t-1); issue half 1 -> full1(t)
-//   workers: stage(0) -> staged(0); for each tile t: load tile t+1's limbs
-//            into registers; wait full0(t); drain half 0 (free0(t) as soon as
-//            it is in registers); wait full1(t) (the fp16 tile is then free);
-//            convert t+1 -> staged(t+1); drain half 1 (free1(t))
-// Every wait is bounded; a wait that runs out records DOT_ETIMEOUT, the CTA
-// stops after its current tile, and the issuer waits (bounded) for its own
-// products in flight before tensor memory is freed.
+// fixed: m limbs (m <= 64 for S = 1, m <= 128 for S = 2), b: [batch][m],
+// p: [batch][2m].  Warp 16 allocates tensor memory and issues every product
+// (one lane); warp 17 forms the constant K; warps 0..15 are four worker
+// groups.  The CTA's blocks are numbered i = 0, 1, .. over its tiles (CB
+// blocks per tile, CB = ceil(8m / 128)); block i accumulates in tensor-memory
+// unit i mod NU (NU = 4 / S units of S regions) and is finished by group
+// i mod 4.  Hand-offs (mbarriers; arrival counts in warps):
+//   full[g]   block i's products done (tcgen05.commit), g = i mod 4   issuer -> group
+//   free[u]   block i drained into registers (4), u = i mod NU  group -> issuer
+//   carry[s]  block i's carry words in cw[s] (4), s = i mod 4    group -> next group
+//   staged[k] a k-block slot holds the next tile's digits (8)    groups -> issuer
+//   kn        the constant K is ready (1)                        warp 17 -> groups
+// Each barrier's consecutive phases are waited by one and the same party (a
+// group waits full[g] for its blocks i, i + 4, ..; the issuer waits every
+// free, staged phase), so a parity wait can never mistake a phase two back
+// for the one it wants; and no producer can run two phases ahead of its
+// consumer: every re-arm waits (through the others) for the consumer of the
+// previous phase.
+// Every wait is bounded; a wait that runs out records DOT_ETIMEOUT and sets a
+// stop flag that every role checks between blocks (groups agree on it through
+// their barrier), and the issuer waits (bounded) for its own last products
+// before tensor memory is freed.
+// 96 registers a thread at most: the 18 warps spread over the SM's four
+// 16K-register partitions, five of them on two partitions
+template <int S>
 __global__ void __launch_bounds__(TZ_THREADS, 1)
 toeplitz_mma_kernel(const uint32_t *fixed, const uint32_t *b, uint32_t *p, int m, size_t batch,
                     const __grid_constant__ CUtensorMap pmap_param, int use_map, uint32_t *status, uint64_t wait_ns)
 {
+    constexpr int NU = 4 / S;
     extern __shared__ __align__(128) unsigned char tz_smem[];
     // swizzled tiles need a 1024-byte aligned base
     unsigned char *base = tz_smem + ((1024u - (smem_u32(tz_smem) & 1023u)) & 1023u);
-    unsigned char *sT = base;                          // Toeplitz blocks d = 0, 1, 2
-    unsigned char *sA = base + TZ_OFF_A;               // two fp16 k-block buffers
-    unsigned char *sBias = base + TZ_OFF_BIAS;         // bias operands (A then B)
-    uint32_t *out = (uint32_t *)(base + TZ_OFF_OUT);   // staged half tile of product limbs
+    unsigned char *sA = base + TZ_OFF_A;
+    unsigned char *sH = base + TZ_OFF_H;
+    unsigned char *sBias = base + TZ_OFF_BIAS;
     uint32_t *Kn = (uint32_t *)(base + TZ_OFF_KN);
-    uint2 *xch = (uint2 *)(base + TZ_OFF_XCH);
-    uint32_t *carry_h = (uint32_t *)(base + TZ_OFF_CARRY);
+    uint32_t *cw = (uint32_t *)(base + TZ_OFF_CW);
     int32_t *dig = (int32_t *)(base + TZ_OFF_DIG);
     int32_t *pre = (int32_t *)(base + TZ_OFF_PRE);
     uint64_t *bars = (uint64_t *)(base + TZ_OFF_BARS);
-    uint64_t *bar_staged = bars, *bar_full = bars + 2, *bar_free = bars + 4;   // staged: per k-block
-    uint64_t *bar_staged_out = bars + 6, *bar_out_free = bars + 7, *bar_kb1done = bars + 8;
-    uint64_t *bar_kn = bars + 9;   // the constant K is ready
-    uint32_t *tmem_slot = (uint32_t *)(bars + 10);
-    uint32_t *out_flags = tmem_slot + 1;   // bit 0: skip the stores, bit 1: stop after the tile
+    uint64_t *bar_full = bars, *bar_free = bars + 4, *bar_carry = bars + 8, *bar_staged = bars + 12;
+    uint64_t *bar_kn = bars + 20;
+    uint32_t *tmem_slot = (uint32_t *)(bars + 21);
+    volatile uint32_t *stopf = tmem_slot + 1;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool issuer = warp == TZ_WORKERS / 32, storer = warp == TZ_WORKERS / 32 + 1;
+    const bool issuer = warp == TZ_WORKERS / 32, kwarp = warp == TZ_WORKERS / 32 + 1;
     const size_t ntiles = (batch + TZ_M - 1) / TZ_M;
     const CUtensorMap *pmap = use_map ? &pmap_param : nullptr;
-    const int nd = 4 * m;   // digits of each operand
+    const int nd = 4 * m;                       // digits of each operand
+    const int KB = (nd + 127) >> 7;             // k-blocks, and the most diagonals meeting a column block
+    const int CB = (8 * m + 127) >> 7;          // column blocks of 128 (32 limbs)
+    // k-block slot of tile number ts and its staging barrier (phase = use of the slot)
+    auto slot = [&](int ts, int kb) -> unsigned char * { return sA + TZ_KBUF * (S == 1 ? 2 * (ts & 1) + kb : kb); };
+    auto sidx = [&](int ts, int kb) { return S == 1 ? 2 * (ts & 1) + kb : kb; };
+    auto spar = [&](int ts) { return (uint32_t)(S == 1 ? (ts >> 1) & 1 : ts & 1); };
 
     // the fixed operand's digits first (their latency gates the set-up), then
     // the first tile's limbs, in flight during the set-up
     uint32_t dk_word = 0, dp_word = 0;
-    const int kdig = tid;   // TZ_DIGITS <= TZ_THREADS: one digit per thread
-    if (kdig < TZ_DIGITS) {
-        if (kdig < nd) dk_word = fixed[kdig >> 2];
-        if (kdig >= 1 && kdig - 1 < nd) dp_word = fixed[(kdig - 1) >> 2];
+    if (tid <= nd) {
+        if (tid < nd) dk_word = fixed[tid >> 2];
+        if (tid >= 1) dp_word = fixed[(tid - 1) >> 2];
     }
     uint32_t x[16];
-    if (tid < TZ_WORKERS && blockIdx.x < ntiles) tz_load(x, b, m, batch, blockIdx.x, tid);
+    if (tid < TZ_WORKERS && blockIdx.x < ntiles && (warp >> 2) < 2 * KB)
+        tz_unit_load(x, b, m, batch, blockIdx.x, (warp >> 2) >> 1, (warp >> 2) & 1, tid & 127);
     if (issuer) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(smem_u32(tmem_slot)), "r"(512) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
         if (lane == 0) {
-            mbar_init(bar_staged + 0, TZ_WORKERS / 32);   // arrivals per warp
-            mbar_init(bar_staged + 1, TZ_WORKERS / 32);
-            mbar_init(bar_kb1done, 1);
-            mbar_init(bar_full + 0, 1);
-            mbar_init(bar_full + 1, 1);
-            mbar_init(bar_free + 0, TZ_WORKERS / 32);
-            mbar_init(bar_free + 1, TZ_WORKERS / 32);
-            mbar_init(bar_staged_out, TZ_WORKERS / 32);
-            mbar_init(bar_out_free, 1);
+            for (int i = 0; i < 4; ++i) {
+                mbar_init(bar_full + i, 1);
+                mbar_init(bar_free + i, 4);
+                mbar_init(bar_carry + i, 4);
+            }
+            for (int i = 0; i < 8; ++i) mbar_init(bar_staged + i, 8);
             mbar_init(bar_kn, 1);
-            *out_flags = 0u;
+            *stopf = 0u;
             mbar_init_fence();
         }
     }
-    // bias operands: column k = 0 of A holds 3072, of B 4096 (fp16), the rest
-    // 0; rows' k-chunk 0 fills the first rows * 16 bytes of each
-    for (int i = tid; i < (TZ_BIAS_A + TZ_BIAS_B) / 16; i += TZ_THREADS) {
-        const bool in_b = i >= TZ_BIAS_A / 16;
-        const int chunk = in_b ? i - TZ_BIAS_A / 16 : i;
-        const uint32_t first = chunk < (in_b ? 256 : 128) ? (in_b ? 0x6C00u : 0x6A00u) : 0u;
+    // bias operands: column k = 0 of A holds 3072, of B 4096 (fp16), the rest 0
+    for (int i = tid; i < 2 * TZ_BIAS_BYTES / 16; i += TZ_THREADS) {
+        const bool in_b = i >= TZ_BIAS_BYTES / 16;
+        const int chunk = in_b ? i - TZ_BIAS_BYTES / 16 : i;
+        const uint32_t first = chunk < 128 ? (in_b ? 0x6C00u : 0x6A00u) : 0u;
         *reinterpret_cast<uint4 *>(sBias + 16 * i) = make_uint4(first, 0u, 0u, 0u);
     }
     // balanced digits a_k = d_k + [d_{k-1} >= 128] - 256 [d_k >= 128], k <= 4m
-    if (kdig < TZ_DIGITS) {
-        const uint32_t dk = (dk_word >> (8 * (kdig & 3))) & 0xFFu;
-        const uint32_t dp = kdig >= 1 ? (dp_word >> (8 * ((kdig - 1) & 3))) & 0xFFu : 0u;
-        dig[kdig] = (int32_t)dk + (int32_t)(dp >= 128u) - 256 * (int32_t)(dk >= 128u);
+    if (tid <= nd) {
+        const uint32_t dk = tid < nd ? (dk_word >> (8 * (tid & 3))) & 0xFFu : 0u;
+        const uint32_t dp = tid >= 1 ? (dp_word >> (8 * ((tid - 1) & 3))) & 0xFFu : 0u;
+        dig[tid] = (int32_t)dk + (int32_t)(dp >= 128u) - 256 * (int32_t)(dk >= 128u);
     }
     __syncthreads();
-    // 8 shifted copies of the reversed digits as fp16: copy o, entry i = r[i + o]
-    unsigned char *rcopy = sA;   // the operand tile is free until the first conversion
-    for (int i = tid; i < 8 * TZ_RDIG / 2; i += TZ_THREADS) {
-        const int o = i / (TZ_RDIG / 2), e = 2 * (i - o * (TZ_RDIG / 2));
-        int v[2];
+    // the reversed digits Rv(i) = a_{J - i}, J = 128 KB + 127, as eight
+    // interleaved copies: the chunk of Rv(i .. i + 7) at (i / 8) * 128 + (i % 8) * 16
+    {
+        const int J = 128 * KB + 127, L = 128 * KB + 256;
+        for (int i = tid; i < L; i += TZ_THREADS) {
+            int v[8];
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int u = TZ_RTOP - (e + j + o);
-            v[j] = (u >= 0 && u <= nd) ? dig[u] : 0;
-        }
-        *reinterpret_cast<uint32_t *>(rcopy + o * TZ_RCOPY + 2 * e) = tz_pack_signed2(v[0], v[1]);
-    }
-    __syncthreads();
-    if (!storer) {
-        // Toeplitz block d, element (n, k) = a[128 d + n - k] when 0 <= . <= 4m:
-        // each 8-k chunk is one aligned 16-byte run of a shifted copy
-        for (int idx = tid; idx < 3 * 128 * 16; idx += TZ_WORKERS + 32) {
-            const int d = idx / (128 * 16), rem = idx - d * 128 * 16, n = rem & 127, kc = rem >> 7;
-            const int i0 = TZ_RTOP - (128 * d + n - 8 * kc), o = i0 & 7;
-            const uint4 chunk = *reinterpret_cast<const uint4 *>(rcopy + o * TZ_RCOPY + 2 * (i0 - o));
-            *reinterpret_cast<uint4 *>(sT + tz_off(128 * d + n, kc * 8, TZ_TROWS)) = chunk;
+            for (int e = 0; e < 8; ++e) {
+                const int u = J - (i + e);
+                v[e] = (u >= 0 && u <= nd) ? dig[u] : 0;
+            }
+            *reinterpret_cast<uint4 *>(sH + (i >> 3) * 128 + (i & 7) * 16) =
+                make_uint4(tz_pack_signed2(v[0], v[1]), tz_pack_signed2(v[2], v[3]), tz_pack_signed2(v[4], v[5]),
+                           tz_pack_signed2(v[6], v[7]));
         }
     }
-    __syncthreads();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tz_fence_before();
     __syncthreads();
@@ -696,99 +573,241 @@ toeplitz_mma_kernel(const uint32_t *fixed, const uint32_t *b, uint32_t *p, int m
 
     if (issuer) {
         if (lane == 0) {
-            int halves = 0;   // issued, for the final drain
-            int it = 0;
-            const uint32_t i128 = tz_idesc(128), i256 = tz_idesc(256);
-            const uint64_t dT = tz_desc(smem_u32(sT));
-            const uint64_t dbuf[2] = {tz_desc(smem_u32(sA)), tz_desc(smem_u32(sA + TZ_KBUF))};
-            const uint64_t drow = (uint64_t)((128 * 128) >> 4);   // 128 stacked rows
-            const uint64_t dbias_a = tz_desc_plain(smem_u32(sBias), 128);
-            const uint64_t dbias_b = tz_desc_plain(smem_u32(sBias + TZ_BIAS_A), 256);
-            for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-                const uint32_t ph = (uint32_t)(it & 1), pph = (uint32_t)((it - 1) & 1);
-                // k-block kb of this tile sits in buffer kb ^ (it & 1)
-                const uint64_t dkb0 = dbuf[it & 1], dkb1 = dbuf[(it & 1) ^ 1];
-                // half 0: bias -> columns 0-255 (N = 256, resets them);
-                //         kb 0 x blocks d = 0, 1 -> columns 0-255; kb 1 x d = 0 -> 128-255
-                if (!mbar_wait_bounded(bar_staged + 0, ph, wait_ns)) break;
-                if (it > 0 && !mbar_wait_bounded(bar_free + 0, pph, wait_ns)) break;
-                tz_fence_after();
-                tz_mma(tmem, dbias_a, dbias_b, i256, 0u);
-                tz_issue_kblock(tmem, dkb0, dT, i256, 1u);
-                if (!mbar_wait_bounded(bar_staged + 1, ph, wait_ns)) break;
-                tz_fence_after();
-                tz_issue_kblock(tmem + 128, dkb1, dT, i128, 1u);
-                tz_commit(bar_full + 0);
-                ++halves;
-                // half 1: bias -> columns 256-511 (resets them); kb 1 x d = 1, 2 ->
-                //         256-511, after which kb 1's buffer is free; kb 0 x d = 2 -> 256-383
-                if (it > 0 && !mbar_wait_bounded(bar_free + 1, pph, wait_ns)) break;
-                tz_fence_after();
-                tz_mma(tmem + 256, dbias_a, dbias_b, i256, 0u);
-                tz_issue_kblock(tmem + 256, dkb1, dT + drow, i256, 1u);
-                tz_commit(bar_kb1done);
-                tz_issue_kblock(tmem + 256, dkb0, dT + 2 * drow, i128, 1u);
-                tz_commit(bar_full + 1);
-                ++halves;
-            }
-            // drain our own last products (a parity wait on a completed phase
-            // returns at once)
-            if (halves > 0) mbar_wait_bounded(bar_full + ((halves - 1) & 1), (uint32_t)(((halves - 1) >> 1) & 1), wait_ns);
-        }
-        __syncwarp();
-    } else if (storer) {
-        tz_make_k(dig, pre, Kn, m, lane);
-        tz_warp_arrive(bar_kn);
-        if (lane == 0) tz_store_loop(pmap, out, bar_staged_out, bar_out_free, out_flags, m, ntiles, wait_ns);
-        __syncwarp();
-    } else {
-        const int quad = warp & 3, seg = warp >> 2;   // TMEM lane quadrant, 16-limb segment
-        int late = 0;
-        if (blockIdx.x < ntiles) {
-            for (int kb = 0; kb < 2; ++kb) {
-                tz_convert(tz_kbuf(sA, kb, 0), x, kb, tid, m);
-                tz_warp_arrive(bar_staged + kb);
-            }
-        }
-        int it = 0;
-        for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-            const uint32_t ph = (uint32_t)(it & 1);
-            const size_t next = tile + gridDim.x;
-            if (next < ntiles) tz_load(x, b, m, batch, next, tid);
-            late |= !mbar_wait_bounded(bar_full + 0, ph, wait_ns);
-            if (it == 0) late |= !mbar_wait_bounded(bar_kn, 0u, wait_ns);
-            tz_fence_after();
-            int late_out = 0;
-            // stage the next tile: its k-block 0 goes into this tile's k-block 1
-            // buffer as soon as the products reading that are done (in the middle
-            // of the half-0 epilogue), its k-block 1 into this tile's k-block 0
-            // buffer once the whole tile is done
-            auto stage_kb0 = [&](int &lt) {
-                if (next < ntiles) {
-                    lt |= !mbar_wait_bounded(bar_kb1done, ph, wait_ns);
-                    tz_convert(tz_kbuf(sA, 0, it + 1), x, 0, tid, m);
-                    tz_warp_arrive(bar_staged + 0);
+            const uint32_t i128 = tz_idesc(128);
+            const uint64_t dH = tz_desc_hankel(smem_u32(sH));
+            const uint64_t dba = tz_desc_plain(smem_u32(sBias), 128);
+            const uint64_t dbb = tz_desc_plain(smem_u32(sBias + TZ_BIAS_BYTES), 128);
+            int i = 0, last = -1;
+            bool ok = true;
+            for (int ts = 0; ok; ++ts) {
+                const size_t tile = blockIdx.x + (size_t)ts * gridDim.x;
+                if (tile >= ntiles) break;
+                for (int cb = 0; cb < CB && ok; ++cb, ++i) {
+                    const int u = i % NU, use = i / NU;
+                    if (*stopf || (use > 0 && !mbar_wait_bounded(bar_free + u, (uint32_t)((use - 1) & 1), wait_ns))) {
+                        ok = false;
+                        break;
+                    }
+                    tz_fence_after();
+#pragma unroll
+                    for (int s = 0; s < S; ++s) tz_mma(tmem + 128 * (u * S + s), dba, dbb, i128, 0u);
+                    const int kb_lo = cb - KB > 0 ? cb - KB : 0, kb_hi = cb < KB - 1 ? cb : KB - 1;
+                    for (int kb = kb_lo; kb <= kb_hi; ++kb) {
+                        if (kb == cb) {   // first block of the tile that reads this k-block
+                            if (!mbar_wait_bounded(bar_staged + sidx(ts, kb), spar(ts), wait_ns)) {
+                                ok = false;
+                                break;
+                            }
+                            tz_fence_after();
+                        }
+                        const int d = cb - kb;
+                        const uint32_t dcol = tmem + 128 * (u * S + (S == 2 ? kb >> 1 : 0));
+                        const uint64_t ad0 = tz_desc(smem_u32(slot(ts, kb)));
+                        const uint64_t bd0 = dH + (uint64_t)((2048 * (KB - d)) >> 4);
+#pragma unroll
+                        for (int st = 0; st < 8; ++st) {
+                            // k = 16 st: atom column st / 4 of A, 32 bytes per step inside it; two
+                            // 8-k chunks of the reversed-digit array (256 bytes) per step
+                            const uint64_t ad = ad0 + (uint64_t)(((st >> 2) * TZ_M * 128 + (st & 3) * 32) >> 4);
+                            const uint64_t bd = bd0 + (uint64_t)((st * 256) >> 4);
+                            tz_mma(dcol, ad, bd, i128, 1u);
+                        }
+                    }
+                    if (!ok) break;
+                    tz_commit(bar_full + (i & 3));
+                    last = i;
                 }
-            };
-            int any_late = tz_epilogue(stage_kb0, tmem, 0, quad, seg, lane, bar_free + 0, Kn, xch, carry_h, out, p, m,
-                                       batch, tile, late, pmap, bar_staged_out, bar_out_free, 2 * it, out_flags,
-                                       late_out, status, wait_ns);
-            late = late_out;
-            late |= !mbar_wait_bounded(bar_full + 1, ph, wait_ns);
-            if (next < ntiles) {
-                tz_convert(tz_kbuf(sA, 1, it + 1), x, 1, tid, m);
-                tz_warp_arrive(bar_staged + 1);
             }
+            if (!ok) {
+                record_status(status, DOT_ETIMEOUT);
+                *stopf = 1u;
+            }
+            // our own products are done before tensor memory is freed (a
+            // parity wait on a completed phase returns at once)
+            if (last >= 0) mbar_wait_bounded(bar_full + (last & 3), (uint32_t)((last >> 2) & 1), wait_ns);
+        }
+        __syncwarp();
+    } else if (kwarp) {
+        tz_make_k(dig, pre, Kn, m, S, lane);
+        tz_warp_arrive(bar_kn);
+    } else {
+        const int g = warp >> 2, quad = warp & 3, j = tid & 127;   // j: the row this thread owns
+        uint32_t *out = (uint32_t *)(base + TZ_OFF_OUT + g * TZ_BOX);
+        int late = 0;
+        // the first tile's digits: unit un (k-block un / 2, row half un % 2) by
+        // group un mod 4 (the first unit's limbs were loaded at entry)
+        if (blockIdx.x < ntiles) {
+            for (int un = g; un < 2 * KB; un += 4) {
+                if (un != g) tz_unit_load(x, b, m, batch, blockIdx.x, un >> 1, un & 1, j);
+                tz_unit_convert(slot(0, un >> 1), x, un >> 1, un & 1, j, m);
+                tz_warp_arrive(bar_staged + sidx(0, un >> 1));
+            }
+        }
+        // Conversion duty of block i: the units of the next tile whose slot
+        // the block's products free -- up to 64 limbs the next tile's units
+        // spread over the tile's blocks, up to 128 limbs k-block kb once the
+        // last block that reads it (kb + KB, or the tile's last) is done.  A
+        // block converts right after its products are done (the slot is then
+        // free), from limbs loaded at the end of the group's previous block.
+        auto duty = [&](int i, int un) {
+            const int ts = i / CB, cb = i - ts * CB;
+            if (blockIdx.x + (size_t)(ts + 1) * gridDim.x >= ntiles) return false;
+            if (S == 1) return un % CB == cb;
+            const int kb = un >> 1, cl = kb + KB < CB - 1 ? kb + KB : CB - 1;
+            return cl == cb;
+        };
+        auto first_duty = [&](int i) {
+            int un = 0;
+            while (un < 2 * KB && !duty(i, un)) ++un;
+            return un;
+        };
+        int xun = first_duty(g);   // the unit whose limbs x holds (2 KB: none)
+        if (xun < 2 * KB) tz_unit_load(x, b, m, batch, blockIdx.x + gridDim.x * (size_t)(g / CB + 1), xun >> 1, xun & 1, j);
+        late |= !mbar_wait_bounded(bar_kn, 0u, wait_ns);
+        for (int i = g;; i += 4) {
+            const int ts = i / CB, cb = i - ts * CB;
+            const size_t tile = blockIdx.x + (size_t)ts * gridDim.x;
+            if (tile >= ntiles) break;
+            const int u = i % NU;
+            // the staging box is free once this group's previous store has read it;
+            // the group agrees on stopping here (a named barrier must never be
+            // left short of its participants)
+            if (j == 0 && pmap) tz_bulk_wait_read();
+            if (tz_group_sync_or(g, (int)*stopf)) break;
+            late |= !mbar_wait_bounded(bar_full + g, (uint32_t)((i >> 2) & 1), wait_ns);
             tz_fence_after();
-            any_late |= tz_epilogue([](int &) {}, tmem, 1, quad, seg, lane, bar_free + 1, Kn, xch + 4 * TZ_M, carry_h, out, p, m,
-                                    batch, tile, late, pmap, bar_staged_out, bar_out_free, 2 * it + 1, out_flags,
-                                    late_out, status, wait_ns);
-            late = late_out;   // carried into the next tile's first vote
-            if (any_late) {   // the same for every worker (barrier vote)
-                if (tid == 0) record_status(status, DOT_ETIMEOUT);
+            // drain the block, 32 columns (8 limbs) per pass; tensor-memory column
+            // 127 - c of a region holds the block's column c.  One slice: the
+            // next pass's columns load while this pass is summed.
+            uint32_t hi = 0, all1 = DOT_FULL, o0 = 0;
+            const uint32_t trow = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(128 * u * S);
+            auto limbs = [&](const uint32_t (&v)[32], int pass) {
+                const uint4 k0 = *reinterpret_cast<const uint4 *>(Kn + 32 * cb + 8 * pass);
+                const uint4 k1 = *reinterpret_cast<const uint4 *>(Kn + 32 * cb + 8 * pass + 4);
+                const uint32_t kk[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
+                uint32_t o[8];
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) {
+                    // limb 8 pass + jj: columns 4 jj + q of the pass sit in register 31 - 4 jj - q
+                    const uint64_t L = (uint64_t)kk[jj] + v[31 - 4 * jj] + (uint64_t)v[30 - 4 * jj] * 256u +
+                                       (uint64_t)v[29 - 4 * jj] * 65536u + (uint64_t)v[28 - 4 * jj] * 16777216u;
+                    const uint64_t acc = L + hi;
+                    o[jj] = (uint32_t)acc;
+                    hi = (uint32_t)(acc >> 32);
+                }
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj)
+                    if (pass > 0 || jj > 0) all1 &= o[jj];
+                if (pass == 0) o0 = o[0];
+                *reinterpret_cast<uint4 *>(tz_stage(out, j, 2 * pass)) = make_uint4(o[0], o[1], o[2], o[3]);
+                *reinterpret_cast<uint4 *>(tz_stage(out, j, 2 * pass + 1)) = make_uint4(o[4], o[5], o[6], o[7]);
+            };
+            if (S == 1) {
+                uint32_t va[32], vb[32];
+                tz_ld32(trow + 96, va);
+                tz_ld_wait(va);
+                tz_ld32(trow + 64, vb);
+                limbs(va, 0);
+                tz_ld_wait(vb);
+                tz_ld32(trow + 32, va);
+                limbs(vb, 1);
+                tz_ld_wait(va);
+                tz_ld32(trow, vb);
+                limbs(va, 2);
+                tz_ld_wait(vb);
+                limbs(vb, 3);
+            } else {
+                // two slices: each pass sums 16-column halves of both regions
+#pragma unroll
+                for (int pass = 0; pass < 4; ++pass) {
+                    uint32_t v[32];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        // columns 16 h .. 16 h + 15 of the pass sit at tensor-memory
+                        // columns 127 - 32 pass - 16 h - 15 .. 127 - 32 pass - 16 h
+                        uint32_t a0[16], a1[16];
+                        const uint32_t taddr = trow + (uint32_t)(112 - 32 * pass - 16 * h);
+                        tz_ld16(taddr, a0);
+                        tz_ld16(taddr + 128, a1);
+                        tz_ld_wait16x2(a0, a1);
+                        // register r of the 16 holds pass column 16 h + 15 - r, which
+                        // the 32-column order keeps in register 31 - (16 h + 15 - r)
+#pragma unroll
+                        for (int r = 0; r < 16; ++r) v[16 - 16 * h + r] = a0[r] + a1[r];
+                    }
+                    limbs(v, pass);
+                }
+            }
+            // all of this thread's columns are in registers: the tensor core may refill the unit
+            tz_fence_before();
+            tz_warp_arrive(bar_free + u);
+            // conversion duty: the next tile's digits into the slots this block frees
+            if (xun < 2 * KB) {
+                tz_unit_convert(slot(ts + 1, xun >> 1), x, xun >> 1, xun & 1, j, m);
+                tz_warp_arrive(bar_staged + sidx(ts + 1, xun >> 1));
+                for (int un = xun + 1; un < 2 * KB; ++un) {
+                    if (!duty(i, un)) continue;
+                    tz_unit_load(x, b, m, batch, tile + gridDim.x, un >> 1, un & 1, j);
+                    tz_unit_convert(slot(ts + 1, un >> 1), x, un >> 1, un & 1, j, m);
+                    tz_warp_arrive(bar_staged + sidx(ts + 1, un >> 1));
+                }
+            }
+            // the carry word from the previous block (every block waits, so that
+            // the carry barriers stay in step; a tile's first block ignores it)
+            uint32_t cin = 0;
+            if (i > 0) {
+                const int pi = i - 1;
+                late |= !mbar_wait_bounded(bar_carry + (pi & 3), (uint32_t)((pi >> 2) & 1), wait_ns);
+                if (cb != 0) cin = cw[(pi & 3) * TZ_M + j];
+            }
+            const uint64_t s0 = (uint64_t)o0 + cin;
+            const uint32_t rip = (uint32_t)(s0 >> 32);
+            tz_stage(out, j, 0)[0] = (uint32_t)s0;
+            if (rip) {   // rare: the carry runs through limbs that are all ones
+                for (int l = 1; l < 32; ++l) {
+                    uint32_t *q = tz_stage(out, j, l >> 2) + (l & 3);
+                    const uint32_t xv = *q;
+                    *q = xv + 1u;
+                    if (xv != DOT_FULL) break;
+                }
+            }
+            cw[(i & 3) * TZ_M + j] = hi + (rip & (all1 == DOT_FULL ? 1u : 0u));
+            tz_warp_arrive(bar_carry + (i & 3));
+            // store the block: one tensor store of 32 limbs x 128 rows, or plain
+            // stores of each thread's own row
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const int any_late = tz_group_sync_or(g, late);
+            if (!any_late) {
+                if (pmap) {
+                    if (j == 0) tz_tma_store(pmap, out, 32 * cb, (int)(tile * TZ_M));
+                } else {
+                    const size_t op = tile * TZ_M + j;
+                    if (op < batch) {
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            const uint4 vv = *reinterpret_cast<const uint4 *>(tz_stage(out, j, c));
+                            const uint32_t e4[4] = {vv.x, vv.y, vv.z, vv.w};
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int l = 32 * cb + 4 * c + e;
+                                if (l < 2 * m) st_stream1(p + op * (size_t)(2 * m) + l, e4[e]);
+                            }
+                        }
+                    }
+                }
+            } else {
+                if (j == 0) record_status(status, DOT_ETIMEOUT);
+                *stopf = 1u;
                 break;
             }
+            // limbs of the group's next block's first duty unit
+            xun = first_duty(i + 4);
+            if (xun < 2 * KB) {
+                const int ts4 = (i + 4) / CB;
+                tz_unit_load(x, b, m, batch, blockIdx.x + gridDim.x * (size_t)(ts4 + 1), xun >> 1, xun & 1, j);
+            }
         }
+        if (j == 0 && pmap) tz_bulk_wait_all();
     }
     tz_fence_before();
     __syncthreads();
@@ -907,15 +926,21 @@ DOT_API dot_status_t dot_mul_shared(dot_ctx_t ctx, const uint32_t *fixed, const 
     if (any_overlap(p, out, b, in) || any_overlap(p, out, fixed, m * 4)) return DOT_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     if (use_tensor_cores) {
-        if (cudaFuncSetAttribute((const void *)toeplitz_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 TZ_SMEM) != cudaSuccess)
+        // up to 64 limbs one K slice (256 digits), up to 128 limbs two
+        const bool split = m > 64;
+        const void *fn = split ? (const void *)toeplitz_mma_kernel<2> : (const void *)toeplitz_mma_kernel<1>;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TZ_SMEM) != cudaSuccess)
             return DOT_ECUDA;
         const size_t ntiles = (batch + TZ_M - 1) / TZ_M;
         const unsigned grid = (unsigned)(ntiles < (size_t)ctx->num_sms ? ntiles : (size_t)ctx->num_sms);
         CUtensorMap map;
         const int use_map = tz_make_map(&map, p, m, batch) ? 1 : 0;
-        toeplitz_mma_kernel<<<grid, TZ_THREADS, TZ_SMEM, st>>>(fixed, b, p, (int)m, batch, map, use_map,
-                                                              ctx->d_status, ctx->wait_limit_ns);
+        if (split)
+            toeplitz_mma_kernel<2><<<grid, TZ_THREADS, TZ_SMEM, st>>>(fixed, b, p, (int)m, batch, map, use_map,
+                                                                     ctx->d_status, ctx->wait_limit_ns);
+        else
+            toeplitz_mma_kernel<1><<<grid, TZ_THREADS, TZ_SMEM, st>>>(fixed, b, p, (int)m, batch, map, use_map,
+                                                                     ctx->d_status, ctx->wait_limit_ns);
         return cudaGetLastError() == cudaSuccess ? DOT_OK : DOT_ECUDA;
     }
     dot_plan_t pl;
