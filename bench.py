@@ -626,7 +626,8 @@ def row_c3(ctx, timer, pk, reps=20):
             roof["bound"] = "latency (too little work per launch for either pipe)"
         sizes[f"{32 * m}_bit"] = {"m_limbs": m, "ops": n, "ms": round(mean, 4), "ms_median": round(med, 4),
                                   "gop_s": round(n / (mean * 1e-3) / 1e9, 4),
-                                  "cols_per_lane": int(dot.plan(dot.OP_MUL, m, n).seg_limbs),
+                                  "kernel": ("one product per thread" if dot.plan(dot.OP_MUL, m, n).kernel == 4
+                                             else f"column sums, {dot.plan(dot.OP_MUL, m, n).seg_limbs} columns per lane"),
                                   "roofline": roof, "bit_exact": ok, "cpu_baseline": cpu}
         del a, b, p
     return {"workload": "2^16 pairs at 256/1024/4096/8192 bits, uniform limbs + 10% both-all-ones pairs",

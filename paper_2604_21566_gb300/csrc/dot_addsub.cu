@@ -511,16 +511,23 @@ static cudaError_t launch_warp(dot_ctx_t ctx, const dot_plan_t &pl, const uint32
 {
     const int lpo = pl.lanes_per_op, nch = pl.chunks;
     const int opw = 32 / lpo;
-    const int U = (nch == 1) ? 4 : 1;
+    // Four op groups per warp keep bytes in flight on large batches; a batch
+    // that would then occupy fewer than 8 warps per SM takes one group per
+    // warp instead, so that every SM works on it (a call that small is one
+    // memory round trip, bound by latency).
+    const bool spread = nch == 1 && dot_ceil_div(batch, (size_t)opw * 4) < (size_t)ctx->num_sms * 8;
+    const int U = (nch == 1 && !spread) ? 4 : 1;
     const size_t warp_iters = dot_ceil_div(batch, (size_t)opw * U);
     const size_t blocks_needed = dot_ceil_div(warp_iters, WARP_KERNEL_THREADS / 32);
     const void *fn;
-    if (nch == 1) fn = (const void *)addsub_warp_kernel<SUB, SEG, 1, 4>;
+    if (nch == 1) fn = spread ? (const void *)addsub_warp_kernel<SUB, SEG, 1, 1> : (const void *)addsub_warp_kernel<SUB, SEG, 1, 4>;
     else if (nch == 2) fn = (const void *)addsub_warp_kernel<SUB, SEG, 2, 1>;
     else fn = (const void *)addsub_warp_kernel<SUB, SEG, 4, 1>;
     const size_t cap = (size_t)ctx->num_sms * dot_blocks_per_sm(fn, WARP_KERNEL_THREADS, 0);
     const unsigned grid = (unsigned)(blocks_needed < cap ? blocks_needed : cap);
-    if (nch == 1)
+    if (nch == 1 && spread)
+        addsub_warp_kernel<SUB, SEG, 1, 1><<<grid, WARP_KERNEL_THREADS, 0, st>>>(a, b, s, cout, m, batch, lpo, nch);
+    else if (nch == 1)
         addsub_warp_kernel<SUB, SEG, 1, 4><<<grid, WARP_KERNEL_THREADS, 0, st>>>(a, b, s, cout, m, batch, lpo, nch);
     else if (nch == 2)
         addsub_warp_kernel<SUB, SEG, 2, 1><<<grid, WARP_KERNEL_THREADS, 0, st>>>(a, b, s, cout, m, batch, lpo, nch);

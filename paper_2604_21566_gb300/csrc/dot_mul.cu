@@ -117,6 +117,101 @@ mul_ragged_kernel(const uint32_t *a, const uint32_t *b, uint32_t *p, const uint6
     }
 }
 
+// ------------------------------------------------ one product per thread
+// Operands of at most 16 limbs: each thread multiplies one pair held in
+// registers (no shared memory, no warp collectives, so a launch of a few
+// thousand products is one memory round trip).  Column c = i + j of the
+// product collects x_i y_j in two three-word sums, over even and odd i (two
+// independent add chains), and one carry pass turns the columns into the
+// 2m limbs in order (Alg. 2 Phases 2-5 within one thread).  M >= m at compile
+// time; limbs past m read as 0.
+__device__ __forceinline__ void add3w(uint32_t &s0, uint32_t &s1, uint32_t &s2, uint32_t t0, uint32_t t1, uint32_t t2)
+{
+    asm("add.cc.u32 %0, %0, %3;\n\taddc.cc.u32 %1, %1, %4;\n\taddc.u32 %2, %2, %5;"
+        : "+r"(s0), "+r"(s1), "+r"(s2) : "r"(t0), "r"(t1), "r"(t2));
+}
+
+template <int M>
+__global__ void __launch_bounds__(256)
+mul_thread_kernel(const uint32_t *a, const uint32_t *b, uint32_t *p, int m, size_t batch, int vec_in, int vec_out)
+{
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t op = (size_t)blockIdx.x * blockDim.x + threadIdx.x; op < batch; op += stride) {
+        uint32_t x[M], y[M];
+        const uint32_t *ar = a + op * (size_t)m, *br = b + op * (size_t)m;
+        if (vec_in) {   // m % 4 == 0 and 16-byte aligned rows
+#pragma unroll
+            for (int q = 0; q < M / 4; ++q) {
+                uint4 u = make_uint4(0u, 0u, 0u, 0u), v = u;
+                if (4 * q < m) {
+                    u = ld_stream4(ar + 4 * q);
+                    v = ld_stream4(br + 4 * q);
+                }
+                x[4 * q] = u.x; x[4 * q + 1] = u.y; x[4 * q + 2] = u.z; x[4 * q + 3] = u.w;
+                y[4 * q] = v.x; y[4 * q + 1] = v.y; y[4 * q + 2] = v.z; y[4 * q + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+                x[i] = i < m ? ld_stream1(ar + i) : 0u;
+                y[i] = i < m ? ld_stream1(br + i) : 0u;
+            }
+        }
+        uint32_t o[2 * M];
+        uint32_t c0 = 0, c1 = 0, c2 = 0;   // carry into the column, three words
+#pragma unroll
+        for (int c = 0; c < 2 * M - 1; ++c) {
+            uint32_t e0 = 0, e1 = 0, e2 = 0, d0 = 0, d1 = 0, d2 = 0;
+#pragma unroll
+            for (int i = (c - M + 1 > 0 ? c - M + 1 : 0); i <= (c < M - 1 ? c : M - 1); ++i) {
+                if (i & 1) mac1(d0, d1, d2, x[i], y[c - i]);
+                else mac1(e0, e1, e2, x[i], y[c - i]);
+            }
+            add3w(c0, c1, c2, e0, e1, e2);
+            add3w(c0, c1, c2, d0, d1, d2);
+            o[c] = c0;
+            c0 = c1;
+            c1 = c2;
+            c2 = 0;
+        }
+        o[2 * M - 1] = c0;
+        uint32_t *pr = p + op * 2 * (size_t)m;
+        if (vec_out) {   // 2m % 4 == 0 and 16-byte aligned rows
+#pragma unroll
+            for (int q = 0; q < M / 2; ++q)
+                if (4 * q < 2 * m) st_stream4(pr + 4 * q, make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]));
+        } else {
+#pragma unroll
+            for (int c = 0; c < 2 * M; ++c)
+                if (c < 2 * m) st_stream1(pr + c, o[c]);
+        }
+    }
+}
+
+template <int M>
+static dot_status_t launch_mul_thread(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b, uint32_t *p, size_t m,
+                                      size_t batch, cudaStream_t st)
+{
+    const void *fn = (const void *)mul_thread_kernel<M>;
+    const bool vec_in = (m % 4 == 0) && aligned16(a) && aligned16(b);
+    const bool vec_out = (m % 2 == 0) && aligned16(p);
+    const size_t need = dot_ceil_div(batch, (size_t)256);
+    const size_t cap = (size_t)ctx->num_sms * dot_blocks_per_sm(fn, 256, 0);
+    const unsigned grid = (unsigned)(need < cap ? need : cap);
+    mul_thread_kernel<M><<<grid, 256, 0, st>>>(a, b, p, (int)m, batch, vec_in, vec_out);
+    return cudaGetLastError() == cudaSuccess ? DOT_OK : DOT_ECUDA;
+}
+
+static dot_status_t launch_mul_thread_any(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b, uint32_t *p,
+                                          size_t m, size_t batch, cudaStream_t st)
+{
+    if (m <= 2) return launch_mul_thread<2>(ctx, a, b, p, m, batch, st);
+    if (m <= 4) return launch_mul_thread<4>(ctx, a, b, p, m, batch, st);
+    if (m <= 8) return launch_mul_thread<8>(ctx, a, b, p, m, batch, st);
+    if (m <= 12) return launch_mul_thread<12>(ctx, a, b, p, m, batch, st);
+    return launch_mul_thread<16>(ctx, a, b, p, m, batch, st);
+}
+
 // ------------------------------------------------------------- launchers
 template <int R, bool SQR = false>
 static dot_status_t launch_mul_batched(dot_ctx_t ctx, const dot_plan_t &pl, const uint32_t *a,
@@ -175,6 +270,7 @@ DOT_API dot_status_t dot_mul(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b
     rc = dot_make_plan(DOT_OP_MUL, m, batch, true, &pl, ctx->tune[DOT_OP_MUL][dot_tune_bucket(m)]);
     if (rc != DOT_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
+    if (pl.kernel == DOT_K_MUL_THREAD) return launch_mul_thread_any(ctx, a, b, p, m, batch, st);
     switch (pl.seg_limbs) {
     case 4: return launch_mul_batched<4>(ctx, pl, a, b, p, m, batch, st);
     case 8: return launch_mul_batched<8>(ctx, pl, a, b, p, m, batch, st);
@@ -200,6 +296,7 @@ DOT_API dot_status_t dot_sqr(dot_ctx_t ctx, const uint32_t *a, uint32_t *p, size
     rc = dot_make_plan(DOT_OP_MUL, m, batch, true, &pl, knob ? knob : dot_mul_cols(m, true));
     if (rc != DOT_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
+    if (pl.kernel == DOT_K_MUL_THREAD) return launch_mul_thread_any(ctx, a, a, p, m, batch, st);
     // Below 128 limbs the rows near the diagonal, summed one column at a time,
     // cost about what the halving saves (measured against the general
     // product: 0.95x at m = 64, 1.21x at m = 128, 1.46x at m = 256), so small

@@ -12,8 +12,11 @@ enum {
     DOT_K_NONE = 0,
     DOT_K_ADDSUB_WARP = 1,   // whole ops inside one warp (runs of lanes)
     DOT_K_ADDSUB_TILE = 2,   // tiles of 256 threads chained by look-back
-    DOT_K_MUL_COLSUM = 3     // column-block sums + carry resolution
+    DOT_K_MUL_COLSUM = 3,    // column-block sums + carry resolution
+    DOT_K_MUL_THREAD = 4     // one product per thread, operands in registers
 };
+// largest operand (limbs) of the one-product-per-thread multiply
+#define DOT_MUL_THREAD_MAX 16
 
 #define DOT_TILE_THREADS 256
 #define DOT_WARP_MAX_CHUNKS 4
@@ -82,6 +85,15 @@ static inline dot_status_t dot_make_plan(int op, size_t m, size_t batch, bool ve
     if (op == DOT_OP_MUL) {
         if (m == 0) return DOT_OK;
         if (m > DOT_MUL_MAX_LIMBS) return DOT_EUNSUPPORTED;
+        if (m <= DOT_MUL_THREAD_MAX && !(knob && dot_knob_valid(op, m, knob))) {
+            // small operands: one product per thread (a tuned column shape
+            // selects the column-sum kernel instead)
+            pl->kernel = DOT_K_MUL_THREAD;
+            pl->seg_limbs = (int)m;
+            pl->lanes_per_op = 1;
+            pl->chunks = 1;
+            return DOT_OK;
+        }
         const int R = (knob && dot_knob_valid(op, m, knob)) ? knob : dot_mul_cols(m);
         pl->kernel = DOT_K_MUL_COLSUM;
         pl->seg_limbs = R;

@@ -239,9 +239,10 @@ extern "C" DOT_API dot_status_t dot_mul_unsat(dot_ctx_t ctx, const uint32_t *a, 
     if (batch > SIZE_MAX / 8 / n) return DOT_EINVAL;
     const size_t in = n * batch * 4, out = 2 * in;
     if (any_overlap(p, out, a, in) || any_overlap(p, out, b, in)) return DOT_EINVAL;
-    // the column-block shape of the saturated multiply fits the same digit counts
+    // the column-block shape of the saturated multiply fits the same digit
+    // counts (always the column-sum plan, whatever the size)
     dot_plan_t pl;
-    rc = dot_make_plan(DOT_OP_MUL, n, batch, true, &pl);
+    rc = dot_make_plan(DOT_OP_MUL, n, batch, true, &pl, dot_mul_cols(n));
     if (rc != DOT_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     switch (pl.seg_limbs) {

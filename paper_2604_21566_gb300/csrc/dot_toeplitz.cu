@@ -943,8 +943,10 @@ DOT_API dot_status_t dot_mul_shared(dot_ctx_t ctx, const uint32_t *fixed, const 
                                                                      ctx->d_status, ctx->wait_limit_ns);
         return cudaGetLastError() == cudaSuccess ? DOT_OK : DOT_ECUDA;
     }
+    // the column-sum plan (the fixed row is broadcast with stride 0)
     dot_plan_t pl;
-    rc = dot_make_plan(DOT_OP_MUL, m, batch, true, &pl, ctx->tune[DOT_OP_MUL][dot_tune_bucket(m)]);
+    const int knob = ctx->tune[DOT_OP_MUL][dot_tune_bucket(m)];
+    rc = dot_make_plan(DOT_OP_MUL, m, batch, true, &pl, knob ? knob : dot_mul_cols(m));
     if (rc != DOT_OK) return rc;
     switch (pl.seg_limbs) {
     case 4: return launch_shared_int<4>(ctx, pl, fixed, b, p, m, batch, st);

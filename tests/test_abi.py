@@ -54,8 +54,12 @@ def test_plans():
     assert p.kernel == 2 and p.tile_limbs == 4096 and p.tiles == 32
     p = dot.plan(dot.OP_ADD, 513, 3)
     assert p.kernel == 2 and p.tiles == 1
-    # multiply: two column blocks per lane, R columns each
-    for m, R, T in ((8, 4, 2), (32, 8, 4), (128, 8, 16), (256, 8, 32), (512, 16, 32), (100, 8, 13),
+    # multiply: up to 16 limbs one product per thread
+    for m in (1, 5, 8, 16):
+        p = dot.plan(dot.OP_MUL, m, 1000)
+        assert (p.kernel, p.lanes_per_op) == (4, 1), m
+    # above: two column blocks per lane, R columns each
+    for m, R, T in ((17, 8, 3), (32, 8, 4), (128, 8, 16), (256, 8, 32), (512, 16, 32), (100, 8, 13),
                     (96, 12, 8), (150, 16, 10), (192, 12, 16), (300, 12, 25), (384, 12, 32), (385, 16, 25)):
         p = dot.plan(dot.OP_MUL, m, 1)
         assert (p.kernel, p.seg_limbs, p.lanes_per_op) == (3, R, T), m
