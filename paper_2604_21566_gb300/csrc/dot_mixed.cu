@@ -7,16 +7,20 @@
 //   2. plan: one warp turns the bucket counts into offsets and work-item
 //      ranges (and clears the counts for the next call);
 //   3. scatter: op indices are written bucket by bucket;
-//   4. run: one persistent kernel; each warp takes work items from a global
-//      counter, heaviest buckets first (longest-processing-time order), and
-//      runs the multiply (column-block sums, Alg. 2) or add/sub (Alg. 1) code
-//      for the item's ops.  Small multiplies share a warp: a bucket fixes the
+//   4. add/sub: the additions and subtractions (Alg. 1), one warp per op
+//      over the two add/sub buckets, 64 warps per SM so that enough of them
+//      have loads in flight (as one item each behind the products, claimed
+//      one at a time, they ran at a seventh of the memory bandwidth);
+//   5. run: one persistent kernel for the products; each warp takes work
+//      items from a global counter, heaviest buckets first
+//      (longest-processing-time order), and runs the multiply (column-block
+//      sums, Alg. 2) for the item's ops.  Small multiplies share a warp: a bucket fixes the
 //      run width T, and each op of the item takes a run of T lanes.  A bucket
 //      also fixes the columns per lane R, chosen so that an op's ceil(m / R)
 //      lanes fill most of its run: the 257..512-limb range is split at 384
 //      into R = 12 and R = 16 (with R = 16 alone a log-uniform size mix
 //      leaves 28% of those lanes idle, with the split about 15%).
-// The four launches are captured once into a CUDA graph per context; later
+// The five launches are captured once into a CUDA graph per context; later
 // calls only update the graph's kernel-node parameters and replay it.
 #include <stdlib.h>
 #include <string.h>
@@ -50,8 +54,10 @@ struct MixedScratch {
     size_t cap;
     cudaGraphExec_t exec;
     cudaGraph_t graph;
-    cudaGraphNode_t node[4];
+    cudaGraphNode_t node[5];
     int persist_blocks;
+    int as_blocks;
+    cudaEvent_t fork, join;
 };
 
 __host__ __device__ inline int bucket_ops_per_item(int bk)
@@ -181,6 +187,40 @@ __device__ __forceinline__ void mixed_mul_item(const dot_desc_t *desc, const uin
     __syncwarp();
 }
 
+#define MIX_AS_THREADS 256
+#define MIX_AS_BLOCKS_PER_SM 8
+
+// The add/sub ops, in bucket order (long ones first): warp k takes ops k,
+// k + W, ...; the next op's index and descriptor load while the current op
+// runs, so that only the op's own data loads sit on its critical path.
+__global__ void __launch_bounds__(MIX_AS_THREADS)
+mixed_addsub(const dot_desc_t *desc, const uint32_t *order, const MixedMeta *meta, const uint32_t *a,
+             const uint32_t *b, uint32_t *r, uint32_t *carry)
+{
+    const uint32_t n = meta->n[BK_ASL] + meta->n[BK_ASS], base = meta->base[BK_ASL];
+    const size_t wg = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const size_t nw = ((size_t)gridDim.x * blockDim.x) >> 5;
+    size_t k = wg;
+    uint32_t op = 0;
+    dot_desc_t d{};
+    if (k < n) {
+        op = order[base + k];
+        d = desc[op];
+    }
+    for (; k < n; k += nw) {
+        const uint32_t cur = op;
+        const dot_desc_t dc = d;
+        if (k + nw < n) {   // prefetch the next op's index and descriptor
+            op = order[base + k + nw];
+            d = desc[op];
+        }
+        if (dc.op == DOT_OP_SUB)
+            addsub_warp_op<true>(a + dc.a_off, b + dc.b_off, r + dc.r_off, dc.m, carry + cur, dc.m, 0u);
+        else
+            addsub_warp_op<false>(a + dc.a_off, b + dc.b_off, r + dc.r_off, dc.m, carry + cur, dc.m, 0u);
+    }
+}
+
 __global__ void __launch_bounds__(MIX_WARPS * 32)
 mixed_run(const dot_desc_t *desc, const uint32_t *order, MixedMeta *meta, const uint32_t *a,
           const uint32_t *b, uint32_t *r, uint32_t *carry)
@@ -188,7 +228,7 @@ mixed_run(const dot_desc_t *desc, const uint32_t *order, MixedMeta *meta, const 
     __shared__ __align__(16) uint32_t smem[MIX_WARPS * MIX_REGION_WORDS];
     const int lane = (int)lane_id(), warp = (int)(threadIdx.x >> 5);
     uint32_t *wsmem = smem + warp * MIX_REGION_WORDS;
-    const uint32_t total = meta->item_base[NBK];
+    const uint32_t total = meta->item_base[BK_ASL];   // the product buckets come first
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(&meta->next_item, 1ull);
@@ -206,15 +246,7 @@ mixed_run(const dot_desc_t *desc, const uint32_t *order, MixedMeta *meta, const 
         case BK_M8C: mixed_mul_item<8, 32>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
         case BK_M8B: mixed_mul_item<8, 16>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
         case BK_M8A: mixed_mul_item<8, 8>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
-        case BK_M4: mixed_mul_item<4, 4>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
-        default: {
-            const uint32_t op = order[base + k0];
-            const dot_desc_t d = desc[op];
-            if (d.op == DOT_OP_SUB)
-                addsub_warp_op<true>(a + d.a_off, b + d.b_off, r + d.r_off, d.m, carry + op, d.m, 0u);
-            else
-                addsub_warp_op<false>(a + d.a_off, b + d.b_off, r + d.r_off, d.m, carry + op, d.m, 0u);
-        }
+        default: mixed_mul_item<4, 4>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
         }
     }
     // the last warp out clears the work counter for the next call
@@ -240,6 +272,7 @@ struct MixedArgs {
     const uint32_t *a, *b;
 };
 
+// p3 serves both the add/sub and the run kernel (the same parameter list)
 static void fill_params(const MixedArgs &A, void **p0, void **p1, void **p2, void **p3)
 {
     // pointers to the argument values of the four kernels (must outlive the call)
@@ -256,7 +289,15 @@ static dot_status_t mixed_prepare(dot_ctx_t ctx, MixedScratch *S, size_t nops)
     if (S->meta == nullptr) {
         if (cudaMalloc((void **)&S->meta, sizeof(MixedMeta)) != cudaSuccess) return DOT_ENOMEM;
         if (cudaMemset(S->meta, 0, sizeof(MixedMeta)) != cudaSuccess) return DOT_ECUDA;
+        // the product kernel takes every SM at its full occupancy (with two
+        // blocks per SM instead of three, to leave the add/sub branch room,
+        // the products ran 1.4x slower); the add/sub blocks fill in as the
+        // product blocks finish
         S->persist_blocks = ctx->num_sms * dot_blocks_per_sm((const void *)mixed_run, MIX_WARPS * 32, 0);
+        S->as_blocks = ctx->num_sms * MIX_AS_BLOCKS_PER_SM;
+        if (cudaEventCreateWithFlags(&S->fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&S->join, cudaEventDisableTiming) != cudaSuccess)
+            return DOT_ECUDA;
     }
     if (nops > S->cap) {
         size_t cap = S->cap ? S->cap : 4096;
@@ -284,25 +325,33 @@ static dot_status_t mixed_capture(dot_ctx_t ctx, MixedScratch *S, const MixedArg
     mixed_classify<<<g1, 256, 0, cs>>>(A.desc, A.nops, A.slot, A.meta, A.carry, A.status);
     mixed_plan<<<1, 32, 0, cs>>>(A.meta);
     mixed_scatter<<<g1, 256, 0, cs>>>(A.slot, A.nops, A.meta, A.order);
+    // the add/sub ops (memory-bound) and the products (ALU-bound) are two
+    // parallel branches of the graph, so that their kernels share the SMs
+    cudaStream_t cs2 = ctx->side[1];
+    if (cudaEventRecord(S->fork, cs) != cudaSuccess || cudaStreamWaitEvent(cs2, S->fork, 0) != cudaSuccess)
+        return DOT_ECUDA;
+    mixed_addsub<<<S->as_blocks, MIX_AS_THREADS, 0, cs2>>>(A.desc, A.order, A.meta, A.a, A.b, A.r, A.carry);
     mixed_run<<<S->persist_blocks, MIX_WARPS * 32, 0, cs>>>(A.desc, A.order, A.meta, A.a, A.b, A.r, A.carry);
+    if (cudaEventRecord(S->join, cs2) != cudaSuccess || cudaStreamWaitEvent(cs, S->join, 0) != cudaSuccess)
+        return DOT_ECUDA;
     cudaGraph_t g = nullptr;
     if (cudaStreamEndCapture(cs, &g) != cudaSuccess || !g) return DOT_ECUDA;
     size_t nn = 0;
     cudaGraphNode_t nodes[8];
-    if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess || nn != 4) {
+    if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess || nn != 5) {
         cudaGraphDestroy(g);
         return DOT_ECUDA;
     }
     cudaGraphGetNodes(g, nodes, &nn);
-    const void *fns[4] = {(const void *)mixed_classify, (const void *)mixed_plan,
-                          (const void *)mixed_scatter, (const void *)mixed_run};
+    const void *fns[5] = {(const void *)mixed_classify, (const void *)mixed_plan, (const void *)mixed_scatter,
+                          (const void *)mixed_addsub, (const void *)mixed_run};
     for (size_t i = 0; i < nn; ++i) {
         cudaKernelNodeParams kp;
         if (cudaGraphKernelNodeGetParams(nodes[i], &kp) != cudaSuccess) {
             cudaGraphDestroy(g);
             return DOT_ECUDA;
         }
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < 5; ++k)
             if (kp.func == fns[k]) S->node[k] = nodes[i];
     }
     cudaGraphExec_t ex = nullptr;
@@ -327,6 +376,8 @@ void dot_mixed_release(dot_ctx_t ctx)
     if (!S) return;
     if (S->exec) cudaGraphExecDestroy(S->exec);
     if (S->graph) cudaGraphDestroy(S->graph);
+    if (S->fork) cudaEventDestroy(S->fork);
+    if (S->join) cudaEventDestroy(S->join);
     cudaFree(S->slot);
     cudaFree(S->order);
     cudaFree(S->meta);
@@ -357,12 +408,13 @@ DOT_API dot_status_t dot_mixed_ragged(dot_ctx_t ctx, const dot_desc_t *desc, siz
     void *p0[6], *p1[1], *p2[4], *p3[7];
     fill_params(A, p0, p1, p2, p3);
     const unsigned g1 = (unsigned)((nops + 255) / 256);
-    const void *fns[4] = {(const void *)mixed_classify, (const void *)mixed_plan,
-                          (const void *)mixed_scatter, (const void *)mixed_run};
-    void **params[4] = {p0, p1, p2, p3};
-    const dim3 grids[4] = {dim3(g1), dim3(1), dim3(g1), dim3((unsigned)S->persist_blocks)};
-    const dim3 blocks[4] = {dim3(256), dim3(32), dim3(256), dim3(MIX_WARPS * 32)};
-    for (int k = 0; k < 4; ++k) {
+    const void *fns[5] = {(const void *)mixed_classify, (const void *)mixed_plan, (const void *)mixed_scatter,
+                          (const void *)mixed_addsub, (const void *)mixed_run};
+    void **params[5] = {p0, p1, p2, p3, p3};
+    const dim3 grids[5] = {dim3(g1), dim3(1), dim3(g1), dim3((unsigned)S->as_blocks),
+                           dim3((unsigned)S->persist_blocks)};
+    const dim3 blocks[5] = {dim3(256), dim3(32), dim3(256), dim3(MIX_AS_THREADS), dim3(MIX_WARPS * 32)};
+    for (int k = 0; k < 5; ++k) {
         cudaKernelNodeParams kp;
         memset(&kp, 0, sizeof kp);
         kp.func = (void *)fns[k];
