@@ -44,27 +44,31 @@
 // Kernel layout (one CTA of 18 warps per SM, persistent over tiles of 128
 // operands; output in blocks of 128 columns = 32 limbs):
 //   * Block pipeline: block i of the CTA's sequence (tile-major) accumulates
-//     in tensor-memory unit i mod (4 / S) (S regions of 128 columns; 512
-//     columns in all), and is drained, regrouped and stored by worker group
-//     i mod 4 (four warps, one per tensor-memory lane quadrant, so that each
-//     thread owns one operand row of the block).  The four groups work on
-//     four consecutive blocks at once; the carry word of each row passes from
-//     block to block through shared memory, and only its addition waits for
-//     the previous block.
+//     in tensor-memory unit i mod 2 (S regions of 128 columns each), and is
+//     drained, regrouped and stored by worker group i mod 4 (four warps, one
+//     per tensor-memory lane quadrant, so that each thread owns one operand
+//     row of the block).  The carry word of each row passes from block to
+//     block through shared memory, and only its addition waits for the
+//     previous block.
 //   * One issuer thread issues, per block and region, a rank-one bias product
 //     (3072 x 4096 = M, which also resets the region) and the products of
 //     every k-block that meets the block (tcgen05.mma, M = 128, N = 128,
-//     K = 16), then commits the block to its unit's mbarrier.
-//   * Batch digits are converted to fp16 in k-block slots of 32 KB: up to 64
-//     limbs two slots per tile, alternating between two pairs from tile to
-//     tile; up to 128 limbs one slot per k-block, each refilled with the next
-//     tile's k-block as soon as the last block that reads it is done.  The
-//     group that finished that block converts, so that conversion runs while
-//     the tensor core works on later blocks.
+//     K = 16), then commits the block to its group's mbarrier.
+//   * Batch digits are converted to fp16 by the worker groups.  Up to 64
+//     limbs they are written to tensor memory (tcgen05.st) and the products
+//     read their A operand from there, so that shared memory feeds only the
+//     B operand; the k-block slots of two tiles alternate, and a group
+//     converts its share of the next tile after draining its block.  Up to
+//     128 limbs they go to one shared-memory slot per k-block, refilled with
+//     the next tile's k-block as soon as the last block that reads it has
+//     its products -- by the group of that block, before it drains it.
 //   * Each group stages its block's 32 limbs per row (128-byte swizzle) and
 //     one of its threads writes the block with a tensor store (TMA): one
 //     16 KB box, where per-thread row stores (rows 8m bytes apart) would
 //     split every warp store into 32 partial lines.
+//   * The constant K is formed while the first products run: a prefix scan
+//     of the fixed operand's balanced digits and the per-limb constants by
+//     the worker warps, the normalisation into limbs by warp 17.
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <string.h>
@@ -78,35 +82,51 @@
 #define TZ_M 128                       // operands per tile (MMA M)
 #define TZ_MAX_LIMBS 128
 #define TZ_KBUF (TZ_M * 128 * 2)       // one k-block slot: 128 rows x 128 digits, fp16
-#define TZ_SLOTS 4
-#define TZ_DMAX 4                      // most diagonals (k-blocks) that meet one column block
-#define TZ_HLEN (128 * TZ_DMAX + 256)  // entries of the reversed digit array
-#define TZ_HBYTES (TZ_HLEN * 16)       // its eight interleaved copies
 #define TZ_BIAS_BYTES (128 * 16 * 2)   // one bias operand, 128 x 16 fp16
 #define TZ_DIGITS (4 * TZ_MAX_LIMBS + 1)
-// shared-memory carve-up, from a 1024-byte aligned base
 #define TZ_BOX (TZ_M * 128)            // one staged block: 128 rows x 32 limbs, 128-byte swizzle
-#define TZ_OFF_A 0
-#define TZ_OFF_OUT (TZ_SLOTS * TZ_KBUF)                   // four staging boxes, one per group
-#define TZ_OFF_H (TZ_OFF_OUT + 4 * TZ_BOX)                // interleaved reversed digits
-#define TZ_OFF_BIAS (TZ_OFF_H + TZ_HBYTES)                // bias operands A, B
-#define TZ_OFF_KN (TZ_OFF_BIAS + 2 * TZ_BIAS_BYTES)       // uint32 [2 * TZ_MAX_LIMBS]: K
-#define TZ_OFF_CW (TZ_OFF_KN + 2 * TZ_MAX_LIMBS * 4)      // uint32 [4][128]: carry words
-#define TZ_DIG_WORDS 576                                  // >= TZ_DIGITS + 40, a multiple of 16 words
-#define TZ_OFF_DIG (TZ_OFF_CW + 4 * TZ_M * 4)             // int32 [TZ_DIG_WORDS]: balanced digits
-#define TZ_OFF_PRE (TZ_OFF_DIG + 4 * TZ_DIG_WORDS)         // int32 [TZ_DIG_WORDS]: their prefix sums
-#define TZ_OFF_BARS (TZ_OFF_PRE + 4 * TZ_DIG_WORDS)        // mbarriers, tensor-memory address, flags
-#define TZ_SMEM (1024 + TZ_OFF_BARS + 256)
-static_assert(TZ_DIG_WORDS >= TZ_DIGITS + 40 && TZ_DIG_WORDS % 16 == 0, "digit arrays");
-static_assert(TZ_OFF_H % 128 == 0 && TZ_OFF_BIAS % 128 == 0 && TZ_OFF_KN % 16 == 0 && TZ_OFF_CW % 16 == 0,
-              "operand and vector alignment");
-static_assert(TZ_OFF_BARS % 16 == 0, "mbarriers are 8-byte aligned");
-static_assert(TZ_OFF_OUT % 1024 == 0 && TZ_BOX % 1024 == 0, "swizzled staging boxes");
-static_assert(TZ_SMEM <= 227 * 1024, "shared memory");
+#define TZ_DIG_WORDS 576               // >= TZ_DIGITS + 40, a multiple of 16 words
 // fp32 bits of the accumulator start value M = 1.5 * 2^23 = 3072 * 4096
 #define TZ_MAGIC_BITS 0x4B400000u
+static_assert(TZ_DIG_WORDS >= TZ_DIGITS + 40 && TZ_DIG_WORDS % 16 == 0, "digit arrays");
 static_assert(TZ_DIGITS <= TZ_THREADS, "one balanced digit per thread");
-static_assert(TZ_SMEM <= 227 * 1024, "shared memory");
+
+// Storage for S K slices.  One slice (up to 64 limbs, at most 2 k-blocks):
+// the batch digits live in tensor memory, four k-block slots of 64 columns
+// (two tiles, alternating) after two accumulator units of 128 columns, and
+// each group has two staging boxes in shared memory, so that it stages its
+// next block while the tensor store of the previous one still reads.  Two
+// slices (up to 128 limbs, 4 k-blocks): two accumulator units of 256
+// columns, four k-block slots in shared memory (slot kb holds k-block kb of
+// one tile after another) and one box per group.  Shared memory is carved
+// from a 1024-byte aligned base.
+template <int S>
+struct TzLayout {
+    static constexpr int KBMAX = 2 * S;                   // k-blocks, and the most diagonals per column block
+    static constexpr bool ATM = S == 1;                   // batch digits in tensor memory
+    static constexpr bool ALT = S == 1;                   // slots alternate between tiles
+    static constexpr int NU = 2;                          // accumulator units
+    static constexpr int ACOL = 128 * S * NU;             // tensor-memory column of the digit slots
+    static constexpr int ASLOTS = 4;                      // k-block slots
+    static constexpr int SMEM_SLOTS = ATM ? 0 : ASLOTS;   // of them in shared memory
+    static constexpr int BOXES = ATM ? 2 : 1;             // staging boxes per group
+    static constexpr int HLEN = 128 * KBMAX + 256;        // entries of the reversed digit array
+    static constexpr int OFF_OUT = SMEM_SLOTS * TZ_KBUF;
+    static constexpr int OFF_H = OFF_OUT + 4 * BOXES * TZ_BOX;       // interleaved reversed digits
+    static constexpr int OFF_BIAS = OFF_H + HLEN * 16;               // bias operands A, B
+    static constexpr int OFF_KN = OFF_BIAS + 2 * TZ_BIAS_BYTES;      // uint32 [2 * TZ_MAX_LIMBS]: K
+    static constexpr int OFF_CW = OFF_KN + 2 * TZ_MAX_LIMBS * 4;     // uint32 [4][128]: carry words
+    static constexpr int OFF_DIG = OFF_CW + 4 * TZ_M * 4;            // int32 [TZ_DIG_WORDS]: balanced digits
+    static constexpr int OFF_PRE = OFF_DIG + 4 * TZ_DIG_WORDS;       // int32 [TZ_DIG_WORDS]: prefix sums
+    static constexpr int OFF_BARS = OFF_PRE + 4 * TZ_DIG_WORDS;      // mbarriers, tensor-memory address, flags
+    static constexpr int SMEM = 1024 + OFF_BARS + 256;
+    static_assert(OFF_H % 128 == 0 && OFF_BIAS % 128 == 0 && OFF_KN % 16 == 0 && OFF_CW % 16 == 0,
+                  "operand and vector alignment");
+    static_assert(OFF_BARS % 16 == 0, "mbarriers are 8-byte aligned");
+    static_assert(OFF_OUT % 1024 == 0 && TZ_BOX % 1024 == 0, "swizzled staging boxes");
+    static_assert(SMEM <= 227 * 1024, "shared memory");
+    static_assert(ACOL + (ATM ? 64 * ASLOTS : 0) <= 512, "tensor memory");
+};
 
 // ------------------------------------------------------------ tcgen05 glue
 // Shared-memory matrix descriptor, K-major with the 128-byte swizzle: a tile
@@ -157,6 +177,22 @@ __device__ __forceinline__ void tz_mma(uint32_t dtmem, uint64_t ad, uint64_t bd,
     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
                  :: "r"(dtmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+}
+
+// a * b + c (64-bit c and result)
+__device__ __forceinline__ uint64_t tz_madw(uint32_t a, uint32_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return d;
+}
+
+// the same with the A operand read from tensor memory at atmem
+__device__ __forceinline__ void tz_mma_ta(uint32_t dtmem, uint32_t atmem, uint64_t bd, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
+                 :: "r"(dtmem), "r"(atmem), "l"(bd), "r"(idesc), "r"(acc) : "memory");
 }
 
 __device__ __forceinline__ void tz_commit(uint64_t *bar)
@@ -230,8 +266,10 @@ __device__ __forceinline__ void tz_pin(uint32_t (&r)[32])
 __device__ __forceinline__ void tz_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tz_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// the tensor stores of this thread have read their shared-memory source
-__device__ __forceinline__ void tz_bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// all but the N most recent tensor stores of this thread have read their
+// shared-memory source
+template <int N>
+__device__ __forceinline__ void tz_bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read %0;" :: "n"(N) : "memory"); }
 
 // one 2-D tensor store (box of 32 limbs x 128 rows at limb x, row y) from a
 // 128-byte-swizzled staging box, in this thread's bulk group
@@ -312,15 +350,18 @@ __device__ __forceinline__ int tz_group_sync_or(int g, int v)
     return r;
 }
 
-// Conversion unit (k-block kb, row half rh) of a tile: 64 rows x 32 limbs,
-// 16 limbs per thread of a worker group (thread j: row 64 rh + j / 2, limbs
-// 16 (j % 2) .. + 15 of the k-block).  Rows past the batch read as zero.
+// Conversion unit (k-block kb, half h) of a tile, 16 limbs per thread of a
+// worker group.  Into tensor memory (TM): limbs 16 h .. 16 h + 15 of the
+// k-block for all 128 rows, thread j taking row j (its tensor-memory lane).
+// Into a shared-memory slot: rows 64 h .. 64 h + 63, thread j taking limbs
+// 16 (j % 2) .. + 15 of row 64 h + j / 2.  Rows past the batch read as zero.
+template <bool TM>
 __device__ __forceinline__ void tz_unit_load(uint32_t (&x)[16], const uint32_t *b, int m, size_t batch, size_t tile,
-                                             int kb, int rh, int j)
+                                             int kb, int h, int j)
 {
-    const int row = 64 * rh + (j >> 1);
+    const int row = TM ? j : 64 * h + (j >> 1);
     const size_t op = tile * TZ_M + row;
-    const int l0 = 32 * kb + 16 * (j & 1);
+    const int l0 = 32 * kb + 16 * (TM ? h : j & 1);
     const uint32_t *src = b + op * (size_t)m + l0;
     // volatile: the loads issue here, not next to their first use, so that
     // their latency overlaps the work in between
@@ -337,6 +378,40 @@ __device__ __forceinline__ void tz_unit_load(uint32_t (&x)[16], const uint32_t *
             if (op < batch && l0 + l < m) asm volatile("ld.global.cs.u32 %0, [%1];" : "=r"(x[l]) : "l"(src + l));
         }
     }
+}
+
+// The unit's digits, shifted by -128, as fp16 pairs into tensor memory: the
+// A operand of the tensor-core product read from tensor memory holds row r
+// in lane r, k elements 2c and 2c + 1 in column c (low and high half).  taddr
+// addresses the warp's lane quadrant at the unit's first column.  Digits
+// beyond the operand's 4m enter as 0 (not -128).
+__device__ __forceinline__ void tz_unit_tmem(uint32_t taddr, const uint32_t (&x)[16], int l0, int m)
+{
+    uint32_t w[32];
+    if (l0 + 16 <= m) {
+#pragma unroll
+        for (int l = 0; l < 16; ++l) {
+            w[2 * l] = tz_shifted2(x[l], 0x4140);
+            w[2 * l + 1] = tz_shifted2(x[l], 0x4342);
+        }
+    } else {
+#pragma unroll
+        for (int l = 0; l < 16; ++l) {
+            const bool in = l0 + l < m;
+            w[2 * l] = in ? tz_shifted2(x[l], 0x4140) : 0u;
+            w[2 * l + 1] = in ? tz_shifted2(x[l], 0x4342) : 0u;
+        }
+    }
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+                 "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+                 "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+                 :: "r"(taddr), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]),
+                    "r"(w[7]), "r"(w[8]), "r"(w[9]), "r"(w[10]), "r"(w[11]), "r"(w[12]), "r"(w[13]), "r"(w[14]),
+                    "r"(w[15]), "r"(w[16]), "r"(w[17]), "r"(w[18]), "r"(w[19]), "r"(w[20]), "r"(w[21]),
+                    "r"(w[22]), "r"(w[23]), "r"(w[24]), "r"(w[25]), "r"(w[26]), "r"(w[27]), "r"(w[28]),
+                    "r"(w[29]), "r"(w[30]), "r"(w[31])
+                 : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // The unit's digits, shifted by -128, as fp16 into a k-block slot (128-byte
@@ -360,57 +435,45 @@ __device__ __forceinline__ void tz_unit_convert(unsigned char *slot, const uint3
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// The constant K (one warp): prefix sums of the balanced digits, the per-limb
-// constants c_l = 128 sum_q W_{4l+q} 2^(8q) - S bits(M) 0x01010101 (W_c = sum
-// of a_u over u in [max(0, c - 4m + 1), min(c, 4m)]), and K = sum_{l < 2m}
-// c_l 2^(32 l) as 2m limbs mod 2^(64 m): each lane takes ceil(2m / 32)
-// consecutive limbs through a signed serial carry, then the lanes pass carry
-// words up until they no longer change.  Limbs from 2m on are 0.
-__device__ __forceinline__ void tz_make_k(const int32_t *dig, int32_t *pre, uint32_t *Kn, int m, int S, int lane)
+// The constant K = sum_{l < 2m} c_l 2^(32 l) mod 2^(64 m), with per-limb
+// constants c_l = 128 sum_q W_{4l+q} 2^(8q) - S bits(M) 0x01010101 and W_c the
+// sum of the balanced digits a_u over u in [max(0, c - 4m + 1), min(c, 4m)]
+// (pre[u + 1] = a_0 + .. + a_u).  c_l of one limb:
+__device__ __forceinline__ int64_t tz_limb_const(const int32_t *pre, int l, int nd, int S)
 {
-    const int nd = 4 * m;
-    int loc[17], sum = 0;
+    int64_t k = -(int64_t)S * (int64_t)TZ_MAGIC_BITS * 0x01010101;
 #pragma unroll
-    for (int j = 0; j < 17; ++j) {
-        const int u = 17 * lane + j;
-        loc[j] = u <= nd ? dig[u] : 0;
-        sum += loc[j];
+    for (int q = 0; q < 4; ++q) {
+        const int c = 4 * l + q;
+        const int lo = c - nd + 1 > 0 ? c - nd + 1 : 0, hi = c < nd ? c : nd;
+        const int64_t W = lo <= hi ? (int64_t)(pre[hi + 1] - pre[lo]) : 0;
+        k += W * 128 * ((int64_t)1 << (8 * q));
     }
-    int incl = sum;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += t;
-    }
-    int run = incl - sum;
-#pragma unroll
-    for (int j = 0; j < 17; ++j) {
-        const int u = 17 * lane + j;
-        if (u <= nd + 1) pre[u] = run;
-        run += loc[j];
-    }
-    __syncwarp();
+    return k;
+}
+
+// K as 2m limbs from the c_l (one warp): each lane takes ceil(2m / 32)
+// consecutive limbs through a signed serial carry, then the lanes pass carry
+// words up until they no longer change.  Limbs from 2m on are written 0 by
+// the caller.
+__device__ __forceinline__ void tz_norm_k(const int64_t *ck, uint32_t *Kn, int m, int lane)
+{
     // lane j takes limbs lpl j .. lpl j + lpl - 1, lpl = ceil(2m / 32) <= 8
     const int lpl = (2 * m + 31) >> 5;
+    int64_t kl[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int l = lpl * lane + j;
+        kl[j] = j < lpl && l < 2 * m ? ck[l] : 0;
+    }
     uint32_t t[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
     int64_t acc = 0;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        if (j >= lpl) break;   // the lane's carry word stays in acc
-        const int l = lpl * lane + j;
-        int64_t k = 0;
-        if (l < 2 * m) {
-            k = -(int64_t)S * (int64_t)TZ_MAGIC_BITS * 0x01010101;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int c = 4 * l + q;
-                const int lo = c - nd + 1 > 0 ? c - nd + 1 : 0, hi = c < nd ? c : nd;
-                const int64_t W = lo <= hi ? (int64_t)(pre[hi + 1] - pre[lo]) : 0;
-                k += W * 128 * ((int64_t)1 << (8 * q));
-            }
+        if (j < lpl) {   // past lpl the lane's carry word stays in acc
+            acc = kl[j] + (acc >> 32);
+            t[j] = (uint32_t)acc;
         }
-        acc = k + (acc >> 32);
-        t[j] = (uint32_t)acc;
     }
     const int64_t cw = acc >> 32;   // this lane's carry word with carry-in 0
     uint32_t all = DOT_FULL, any = 0u;
@@ -448,22 +511,31 @@ __device__ __forceinline__ void tz_make_k(const int32_t *dig, int32_t *pre, uint
         const int l = lpl * lane + j;
         if (j < lpl && l < 2 * m) Kn[l] = t[j];
     }
-    // limbs past 2m (the rest of the top column block) are 0
-    for (int l = 2 * m + lane; l < 2 * TZ_MAX_LIMBS; l += 32) Kn[l] = 0u;
 }
+
+// named barriers of the 16 worker warps and warp 17 (544 threads) while they
+// form K: 6 = prefix sums written, 7 = limb constants written
+__device__ __forceinline__ void tz_kbar_sync(int id) { asm volatile("bar.sync %0, 544;" :: "r"(id) : "memory"); }
+__device__ __forceinline__ void tz_kbar_arrive(int id) { asm volatile("bar.arrive %0, 544;" :: "r"(id) : "memory"); }
 
 // fixed: m limbs (m <= 64 for S = 1, m <= 128 for S = 2), b: [batch][m],
 // p: [batch][2m].  Warp 16 allocates tensor memory and issues every product
-// (one lane); warp 17 forms the constant K; warps 0..15 are four worker
+// (one lane); warp 17 normalises the constant K; warps 0..15 are four worker
 // groups.  The CTA's blocks are numbered i = 0, 1, .. over its tiles (CB
 // blocks per tile, CB = ceil(8m / 128)); block i accumulates in tensor-memory
-// unit i mod NU (NU = 4 / S units of S regions) and is finished by group
+// unit i mod NU (NU = 2 units of S regions) and is finished by group
 // i mod 4.  Hand-offs (mbarriers; arrival counts in warps):
 //   full[g]   block i's products done (tcgen05.commit), g = i mod 4   issuer -> group
 //   free[u]   block i drained into registers (4), u = i mod NU  group -> issuer
 //   carry[s]  block i's carry words in cw[s] (4), s = i mod 4    group -> next group
 //   staged[k] a k-block slot holds the next tile's digits (8)    groups -> issuer
 //   kn        the constant K is ready (1)                        warp 17 -> groups
+// k-block slots: one slice alternates two tiles' slots (tensor memory), and
+// a group converts its block's share of the next tile's digits after
+// draining the block; two slices refill slot kb once the tile's last block
+// that reads it has its products, and that block's group converts before it
+// drains.  Either way from limbs loaded at the end of the group's previous
+// block.
 // Each barrier's consecutive phases are waited by one and the same party (a
 // group waits full[g] for its blocks i, i + 4, ..; the issuer waits every
 // free, staged phase), so a parity wait can never mistake a phase two back
@@ -481,18 +553,19 @@ __global__ void __launch_bounds__(TZ_THREADS, 1)
 toeplitz_mma_kernel(const uint32_t *fixed, const uint32_t *b, uint32_t *p, int m, size_t batch,
                     const __grid_constant__ CUtensorMap pmap_param, int use_map, uint32_t *status, uint64_t wait_ns)
 {
-    constexpr int NU = 4 / S;
+    using Lay = TzLayout<S>;
+    constexpr int NU = Lay::NU;
     extern __shared__ __align__(128) unsigned char tz_smem[];
     // swizzled tiles need a 1024-byte aligned base
     unsigned char *base = tz_smem + ((1024u - (smem_u32(tz_smem) & 1023u)) & 1023u);
-    unsigned char *sA = base + TZ_OFF_A;
-    unsigned char *sH = base + TZ_OFF_H;
-    unsigned char *sBias = base + TZ_OFF_BIAS;
-    uint32_t *Kn = (uint32_t *)(base + TZ_OFF_KN);
-    uint32_t *cw = (uint32_t *)(base + TZ_OFF_CW);
-    int32_t *dig = (int32_t *)(base + TZ_OFF_DIG);
-    int32_t *pre = (int32_t *)(base + TZ_OFF_PRE);
-    uint64_t *bars = (uint64_t *)(base + TZ_OFF_BARS);
+    unsigned char *sA = base;
+    unsigned char *sH = base + Lay::OFF_H;
+    unsigned char *sBias = base + Lay::OFF_BIAS;
+    uint32_t *Kn = (uint32_t *)(base + Lay::OFF_KN);
+    uint32_t *cw = (uint32_t *)(base + Lay::OFF_CW);
+    int32_t *dig = (int32_t *)(base + Lay::OFF_DIG);
+    int32_t *pre = (int32_t *)(base + Lay::OFF_PRE);
+    uint64_t *bars = (uint64_t *)(base + Lay::OFF_BARS);
     uint64_t *bar_full = bars, *bar_free = bars + 4, *bar_carry = bars + 8, *bar_staged = bars + 12;
     uint64_t *bar_kn = bars + 20;
     uint32_t *tmem_slot = (uint32_t *)(bars + 21);
@@ -504,10 +577,12 @@ toeplitz_mma_kernel(const uint32_t *fixed, const uint32_t *b, uint32_t *p, int m
     const int nd = 4 * m;                       // digits of each operand
     const int KB = (nd + 127) >> 7;             // k-blocks, and the most diagonals meeting a column block
     const int CB = (8 * m + 127) >> 7;          // column blocks of 128 (32 limbs)
-    // k-block slot of tile number ts and its staging barrier (phase = use of the slot)
-    auto slot = [&](int ts, int kb) -> unsigned char * { return sA + TZ_KBUF * (S == 1 ? 2 * (ts & 1) + kb : kb); };
-    auto sidx = [&](int ts, int kb) { return S == 1 ? 2 * (ts & 1) + kb : kb; };
-    auto spar = [&](int ts) { return (uint32_t)(S == 1 ? (ts >> 1) & 1 : ts & 1); };
+    // k-block slot of tile number ts and its staging barrier (phase = use of
+    // the slot): alternating between tiles, or slot kb
+    constexpr bool alt = Lay::ALT;
+    auto sidx = [&](int ts, int kb) { return alt ? KB * (ts & 1) + kb : kb; };
+    auto slot = [&](int ts, int kb) -> unsigned char * { return sA + TZ_KBUF * sidx(ts, kb); };
+    auto spar = [&](int ts) { return (uint32_t)(alt ? (ts >> 1) & 1 : ts & 1); };
 
     // the fixed operand's digits first (their latency gates the set-up), then
     // the first tile's limbs, in flight during the set-up
@@ -516,9 +591,15 @@ toeplitz_mma_kernel(const uint32_t *fixed, const uint32_t *b, uint32_t *p, int m
         if (tid < nd) dk_word = fixed[tid >> 2];
         if (tid >= 1) dp_word = fixed[(tid - 1) >> 2];
     }
-    uint32_t x[16];
-    if (tid < TZ_WORKERS && blockIdx.x < ntiles && (warp >> 2) < 2 * KB)
-        tz_unit_load(x, b, m, batch, blockIdx.x, (warp >> 2) >> 1, (warp >> 2) & 1, tid & 127);
+    // worker group g = warp / 4 (warps 0..15), its warp's lane quadrant and
+    // the row j a thread owns
+    const int g = warp >> 2, quad = warp & 3, j = tid & 127;
+    // the first tile's units un = g and g + 4 of a worker group
+    uint32_t xa[16], xb[16];
+    if (tid < TZ_WORKERS && blockIdx.x < ntiles) {
+        if (g < 2 * KB) tz_unit_load<Lay::ATM>(xa, b, m, batch, blockIdx.x, g >> 1, g & 1, j);
+        if (g + 4 < 2 * KB) tz_unit_load<Lay::ATM>(xb, b, m, batch, blockIdx.x, (g + 4) >> 1, g & 1, j);
+    }
     if (issuer) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(smem_u32(tmem_slot)), "r"(512) : "memory");
@@ -548,7 +629,37 @@ toeplitz_mma_kernel(const uint32_t *fixed, const uint32_t *b, uint32_t *p, int m
         const uint32_t dp = tid >= 1 ? (dp_word >> (8 * ((tid - 1) & 3))) & 0xFFu : 0u;
         dig[tid] = (int32_t)dk + (int32_t)(dp >= 128u) - 256 * (int32_t)(dk >= 128u);
     }
+    tz_fence_before();
     __syncthreads();
+    tz_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    // unit un (k-block un / 2, half un % 2) of tile number tsn from the limbs
+    // in x, by the four warps of a worker group
+    auto convert = [&](int tsn, int un, const uint32_t (&x)[16]) {
+        const int kb = un >> 1, h = un & 1;
+        if (Lay::ATM)
+            tz_unit_tmem(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(Lay::ACOL + 64 * sidx(tsn, kb) + 32 * h),
+                         x, 32 * kb + 16 * h, m);
+        else
+            tz_unit_convert(slot(tsn, kb), x, kb, h, j, m);
+        tz_fence_before();
+        tz_warp_arrive(bar_staged + sidx(tsn, kb));
+    };
+    // K is formed by the worker warps and warp 17 (scan index ks, 544 threads):
+    // a scan of the balanced digits inside each warp, warp totals into Kn
+    // (free until K itself is written)
+    const bool kthr = tid < TZ_WORKERS || kwarp;
+    const int ks = kwarp ? TZ_WORKERS + lane : tid;
+    int incl = 0;
+    if (kthr) {
+        incl = ks <= nd ? dig[ks] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += t;
+        }
+        if (lane == 31) Kn[ks >> 5] = (uint32_t)incl;
+    }
     // the reversed digits Rv(i) = a_{J - i}, J = 128 KB + 127, as eight
     // interleaved copies: the chunk of Rv(i .. i + 7) at (i / 8) * 128 + (i % 8) * 16
     {
@@ -565,11 +676,30 @@ toeplitz_mma_kernel(const uint32_t *fixed, const uint32_t *b, uint32_t *p, int m
                            tz_pack_signed2(v[6], v[7]));
         }
     }
+    // the first tile's digits: unit un by group un mod 4
+    if (tid < TZ_WORKERS && blockIdx.x < ntiles) {
+        if (g < 2 * KB) convert(0, g, xa);
+        if (g + 4 < 2 * KB) convert(0, g + 4, xb);
+    }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tz_fence_before();
     __syncthreads();
     tz_fence_after();
-    const uint32_t tmem = *tmem_slot;
+    if (kthr) {
+        // prefix sums pre[u + 1] = a_0 + .. + a_u, then the limb constants c_l
+        // (over the digit array, which nothing reads any more) and the zero
+        // limbs of K past 2m
+        int off = 0;
+        for (int w = 0; w < (ks >> 5); ++w) off += (int)Kn[w];
+        if (ks <= nd) pre[ks + 1] = incl + off;
+        if (ks == 0) pre[0] = 0;
+        tz_kbar_sync(6);
+        int64_t *ck = reinterpret_cast<int64_t *>(dig);
+        if (ks < 2 * m) ck[ks] = tz_limb_const(pre, ks, nd, S);
+        else if (ks < 2 * TZ_MAX_LIMBS) Kn[ks] = 0u;
+        if (kwarp) tz_kbar_sync(7);
+        else tz_kbar_arrive(7);
+    }
 
     if (issuer) {
         if (lane == 0) {
@@ -602,15 +732,23 @@ toeplitz_mma_kernel(const uint32_t *fixed, const uint32_t *b, uint32_t *p, int m
                         }
                         const int d = cb - kb;
                         const uint32_t dcol = tmem + 128 * (u * S + (S == 2 ? kb >> 1 : 0));
-                        const uint64_t ad0 = tz_desc(smem_u32(slot(ts, kb)));
                         const uint64_t bd0 = dH + (uint64_t)((2048 * (KB - d)) >> 4);
+                        if (Lay::ATM) {
+                            // k = 16 st: columns 8 st .. 8 st + 7 of the k-block's digits
+                            const uint32_t acol = tmem + Lay::ACOL + 64 * sidx(ts, kb);
 #pragma unroll
-                        for (int st = 0; st < 8; ++st) {
-                            // k = 16 st: atom column st / 4 of A, 32 bytes per step inside it; two
-                            // 8-k chunks of the reversed-digit array (256 bytes) per step
-                            const uint64_t ad = ad0 + (uint64_t)(((st >> 2) * TZ_M * 128 + (st & 3) * 32) >> 4);
-                            const uint64_t bd = bd0 + (uint64_t)((st * 256) >> 4);
-                            tz_mma(dcol, ad, bd, i128, 1u);
+                            for (int st = 0; st < 8; ++st)
+                                tz_mma_ta(dcol, acol + 8 * st, bd0 + (uint64_t)((st * 256) >> 4), i128, 1u);
+                        } else {
+                            const uint64_t ad0 = tz_desc(smem_u32(slot(ts, kb)));
+#pragma unroll
+                            for (int st = 0; st < 8; ++st) {
+                                // k = 16 st: atom column st / 4 of A, 32 bytes per step inside it;
+                                // two 8-k chunks of the reversed-digit array (256 bytes) per step
+                                const uint64_t ad = ad0 + (uint64_t)(((st >> 2) * TZ_M * 128 + (st & 3) * 32) >> 4);
+                                const uint64_t bd = bd0 + (uint64_t)((st * 256) >> 4);
+                                tz_mma(dcol, ad, bd, i128, 1u);
+                            }
                         }
                     }
                     if (!ok) break;
@@ -628,54 +766,64 @@ toeplitz_mma_kernel(const uint32_t *fixed, const uint32_t *b, uint32_t *p, int m
         }
         __syncwarp();
     } else if (kwarp) {
-        tz_make_k(dig, pre, Kn, m, S, lane);
+        tz_norm_k(reinterpret_cast<const int64_t *>(dig), Kn, m, lane);
         tz_warp_arrive(bar_kn);
     } else {
-        const int g = warp >> 2, quad = warp & 3, j = tid & 127;   // j: the row this thread owns
-        uint32_t *out = (uint32_t *)(base + TZ_OFF_OUT + g * TZ_BOX);
         int late = 0;
-        // the first tile's digits: unit un (k-block un / 2, row half un % 2) by
-        // group un mod 4 (the first unit's limbs were loaded at entry)
-        if (blockIdx.x < ntiles) {
-            for (int un = g; un < 2 * KB; un += 4) {
-                if (un != g) tz_unit_load(x, b, m, batch, blockIdx.x, un >> 1, un & 1, j);
-                tz_unit_convert(slot(0, un >> 1), x, un >> 1, un & 1, j, m);
-                tz_warp_arrive(bar_staged + sidx(0, un >> 1));
-            }
-        }
         // Conversion duty of block i: the units of the next tile whose slot
-        // the block's products free -- up to 64 limbs the next tile's units
-        // spread over the tile's blocks, up to 128 limbs k-block kb once the
-        // last block that reads it (kb + KB, or the tile's last) is done.  A
-        // block converts right after its products are done (the slot is then
-        // free), from limbs loaded at the end of the group's previous block.
+        // the block's products free -- alternating slots: the next tile's units
+        // spread over the tile's blocks; slot kb: k-block kb once the last block
+        // that reads it (kb + KB, or the tile's last) has its products.
         auto duty = [&](int i, int un) {
             const int ts = i / CB, cb = i - ts * CB;
             if (blockIdx.x + (size_t)(ts + 1) * gridDim.x >= ntiles) return false;
-            if (S == 1) return un % CB == cb;
+            if (alt) return un % CB == cb;
             const int kb = un >> 1, cl = kb + KB < CB - 1 ? kb + KB : CB - 1;
             return cl == cb;
         };
-        auto first_duty = [&](int i) {
-            int un = 0;
+        auto next_duty = [&](int i, int un) {   // block i's first duty unit from un on (2 KB: none)
             while (un < 2 * KB && !duty(i, un)) ++un;
             return un;
         };
-        int xun = first_duty(g);   // the unit whose limbs x holds (2 KB: none)
-        if (xun < 2 * KB) tz_unit_load(x, b, m, batch, blockIdx.x + gridDim.x * (size_t)(g / CB + 1), xun >> 1, xun & 1, j);
+        // limbs of block i's first two duty units into xa, xb
+        int xu0, xu1;
+        auto prefetch = [&](int i) {
+            xu0 = next_duty(i, 0);
+            xu1 = xu0 < 2 * KB ? next_duty(i, xu0 + 1) : 2 * KB;
+            const size_t tn = blockIdx.x + gridDim.x * (size_t)(i / CB + 1);
+            if (xu0 < 2 * KB) tz_unit_load<Lay::ATM>(xa, b, m, batch, tn, xu0 >> 1, xu0 & 1, j);
+            if (xu1 < 2 * KB) tz_unit_load<Lay::ATM>(xb, b, m, batch, tn, xu1 >> 1, xu1 & 1, j);
+        };
+        prefetch(g);
         late |= !mbar_wait_bounded(bar_kn, 0u, wait_ns);
         for (int i = g;; i += 4) {
             const int ts = i / CB, cb = i - ts * CB;
             const size_t tile = blockIdx.x + (size_t)ts * gridDim.x;
             if (tile >= ntiles) break;
             const int u = i % NU;
-            // the staging box is free once this group's previous store has read it;
-            // the group agrees on stopping here (a named barrier must never be
-            // left short of its participants)
-            if (j == 0 && pmap) tz_bulk_wait_read();
+            uint32_t *out = (uint32_t *)(base + Lay::OFF_OUT +
+                                         (g * Lay::BOXES + (Lay::BOXES == 2 ? (i >> 2) & 1 : 0)) * TZ_BOX);
+            // the staging box is free once the group's store that last used it
+            // has read it; the group agrees on stopping here (a named barrier
+            // must never be left short of its participants)
+            if (j == 0 && pmap) tz_bulk_wait_read<Lay::BOXES - 1>();
             if (tz_group_sync_or(g, (int)*stopf)) break;
             late |= !mbar_wait_bounded(bar_full + g, (uint32_t)((i >> 2) & 1), wait_ns);
             tz_fence_after();
+            // conversion duty: the block's products are done, so the slots it
+            // frees may take the next tile's digits.  Slot kb is needed again
+            // soon: convert before draining; alternating slots are not needed
+            // before the next tile: drain first, so that the unit is free sooner.
+            if (!alt && xu0 < 2 * KB) {
+                convert(ts + 1, xu0, xa);
+                if (xu1 < 2 * KB) {
+                    convert(ts + 1, xu1, xb);
+                    for (int un = next_duty(i, xu1 + 1); un < 2 * KB; un = next_duty(i, un + 1)) {
+                        tz_unit_load<Lay::ATM>(xa, b, m, batch, tile + gridDim.x, un >> 1, un & 1, j);
+                        convert(ts + 1, un, xa);
+                    }
+                }
+            }
             // drain the block, 32 columns (8 limbs) per pass; tensor-memory column
             // 127 - c of a region holds the block's column c.  One slice: the
             // next pass's columns load while this pass is summed.
@@ -685,10 +833,11 @@ toeplitz_mma_kernel(const uint32_t *fixed, const uint32_t *b, uint32_t *p, int m
                 const uint4 k0 = *reinterpret_cast<const uint4 *>(Kn + 32 * cb + 8 * pass);
                 const uint4 k1 = *reinterpret_cast<const uint4 *>(Kn + 32 * cb + 8 * pass + 4);
                 const uint32_t kk[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
+                // limb 8 pass + jj: columns 4 jj + q of the pass sit in register
+                // 31 - 4 jj - q; each limb's sum is formed off the serial carry
                 uint32_t o[8];
 #pragma unroll
                 for (int jj = 0; jj < 8; ++jj) {
-                    // limb 8 pass + jj: columns 4 jj + q of the pass sit in register 31 - 4 jj - q
                     const uint64_t L = (uint64_t)kk[jj] + v[31 - 4 * jj] + (uint64_t)v[30 - 4 * jj] * 256u +
                                        (uint64_t)v[29 - 4 * jj] * 65536u + (uint64_t)v[28 - 4 * jj] * 16777216u;
                     const uint64_t acc = L + hi;
@@ -715,6 +864,9 @@ toeplitz_mma_kernel(const uint32_t *fixed, const uint32_t *b, uint32_t *p, int m
                 tz_ld32(trow, vb);
                 limbs(va, 2);
                 tz_ld_wait(vb);
+                // every column of the block is in registers: the unit may be refilled
+                tz_fence_before();
+                tz_warp_arrive(bar_free + u);
                 limbs(vb, 3);
             } else {
                 // two slices: each pass sums 16-column halves of both regions
@@ -737,19 +889,17 @@ toeplitz_mma_kernel(const uint32_t *fixed, const uint32_t *b, uint32_t *p, int m
                     }
                     limbs(v, pass);
                 }
+                tz_fence_before();
+                tz_warp_arrive(bar_free + u);
             }
-            // all of this thread's columns are in registers: the tensor core may refill the unit
-            tz_fence_before();
-            tz_warp_arrive(bar_free + u);
-            // conversion duty: the next tile's digits into the slots this block frees
-            if (xun < 2 * KB) {
-                tz_unit_convert(slot(ts + 1, xun >> 1), x, xun >> 1, xun & 1, j, m);
-                tz_warp_arrive(bar_staged + sidx(ts + 1, xun >> 1));
-                for (int un = xun + 1; un < 2 * KB; ++un) {
-                    if (!duty(i, un)) continue;
-                    tz_unit_load(x, b, m, batch, tile + gridDim.x, un >> 1, un & 1, j);
-                    tz_unit_convert(slot(ts + 1, un >> 1), x, un >> 1, un & 1, j, m);
-                    tz_warp_arrive(bar_staged + sidx(ts + 1, un >> 1));
+            if (alt && xu0 < 2 * KB) {
+                convert(ts + 1, xu0, xa);
+                if (xu1 < 2 * KB) {
+                    convert(ts + 1, xu1, xb);
+                    for (int un = next_duty(i, xu1 + 1); un < 2 * KB; un = next_duty(i, un + 1)) {
+                        tz_unit_load<Lay::ATM>(xa, b, m, batch, tile + gridDim.x, un >> 1, un & 1, j);
+                        convert(ts + 1, un, xa);
+                    }
                 }
             }
             // the carry word from the previous block (every block waits, so that
@@ -800,12 +950,8 @@ toeplitz_mma_kernel(const uint32_t *fixed, const uint32_t *b, uint32_t *p, int m
                 *stopf = 1u;
                 break;
             }
-            // limbs of the group's next block's first duty unit
-            xun = first_duty(i + 4);
-            if (xun < 2 * KB) {
-                const int ts4 = (i + 4) / CB;
-                tz_unit_load(x, b, m, batch, blockIdx.x + gridDim.x * (size_t)(ts4 + 1), xun >> 1, xun & 1, j);
-            }
+            // limbs of the group's next block's duty units
+            prefetch(i + 4);
         }
         if (j == 0 && pmap) tz_bulk_wait_all();
     }
@@ -929,17 +1075,18 @@ DOT_API dot_status_t dot_mul_shared(dot_ctx_t ctx, const uint32_t *fixed, const 
         // up to 64 limbs one K slice (256 digits), up to 128 limbs two
         const bool split = m > 64;
         const void *fn = split ? (const void *)toeplitz_mma_kernel<2> : (const void *)toeplitz_mma_kernel<1>;
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TZ_SMEM) != cudaSuccess)
+        const int smem = split ? TzLayout<2>::SMEM : TzLayout<1>::SMEM;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
             return DOT_ECUDA;
         const size_t ntiles = (batch + TZ_M - 1) / TZ_M;
         const unsigned grid = (unsigned)(ntiles < (size_t)ctx->num_sms ? ntiles : (size_t)ctx->num_sms);
         CUtensorMap map;
         const int use_map = tz_make_map(&map, p, m, batch) ? 1 : 0;
         if (split)
-            toeplitz_mma_kernel<2><<<grid, TZ_THREADS, TZ_SMEM, st>>>(fixed, b, p, (int)m, batch, map, use_map,
+            toeplitz_mma_kernel<2><<<grid, TZ_THREADS, smem, st>>>(fixed, b, p, (int)m, batch, map, use_map,
                                                                      ctx->d_status, ctx->wait_limit_ns);
         else
-            toeplitz_mma_kernel<1><<<grid, TZ_THREADS, TZ_SMEM, st>>>(fixed, b, p, (int)m, batch, map, use_map,
+            toeplitz_mma_kernel<1><<<grid, TZ_THREADS, smem, st>>>(fixed, b, p, (int)m, batch, map, use_map,
                                                                      ctx->d_status, ctx->wait_limit_ns);
         return cudaGetLastError() == cudaSuccess ? DOT_OK : DOT_ECUDA;
     }
