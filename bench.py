@@ -537,7 +537,8 @@ def _hs(t):
 
 
 def row_peaks():
-    """Integer-pipe ceilings measured on this GPU (libdotprobe)."""
+    """Integer-pipe ceilings and tensor-pipe shape rates measured on this GPU
+    (libdotprobe)."""
     from paper_2604_21566_gb300 import probe
     return probe.measure()
 
@@ -750,6 +751,17 @@ def tz_units_per_tile(m: int) -> int:
     return units
 
 
+def _tc_shape(pk, m, tflops):
+    """The kernel's own product shape issued back to back alone (libdotprobe):
+    M = 128, N = 128, K = 16 with A from tensor memory (up to 64 limbs) or
+    shared memory (two K slices); the widest single-CTA shape beside it."""
+    key = "mma_n128_tmem" if m <= 64 else "mma_n128_smem"
+    shape = pk[key]["per_s"] / 1e12
+    widest = pk["mma_n256_tmem"]["per_s"] / 1e12
+    return {"peak_own_shape": round(shape, 1), "own_shape": key, "frac_of_own_shape": round(tflops / shape, 4),
+            "peak_n256_tmem": round(widest, 1)}
+
+
 def row_c5(ctx, timer, pk, reps=50):
     """Shared operand: one fixed 2048-bit multiplier x 2^16 2048-bit operands,
     Toeplitz product on the tensor cores vs the INT32 paths."""
@@ -787,7 +799,8 @@ def row_c5(ctx, timer, pk, reps=50):
                          "useful_tflop_s": round(useful / (t_tc * 1e-3) / 1e12, 1),
                          "frac_useful": round(useful / (t_tc * 1e-3) / 1e12 / tc_peak, 4),
                          "achieved_GB_s": round(bytes_moved / (t_tc * 1e-3) / 1e9, 1),
-                         "frac_hbm": round(bytes_moved / (t_tc * 1e-3) / 1e9 / hbm, 4)},
+                         "frac_hbm": round(bytes_moved / (t_tc * 1e-3) / 1e9 / hbm, 4),
+                         **_tc_shape(pk, m, tflops)},
             "int32_roofline": _int_roofline(n * m * m, t_int, pk),
             "cpu_baseline": cpu}
 
@@ -823,7 +836,8 @@ def row_n3(ctx, timer, pk, reps=20):
                          "peak_source": f"{src} bf16 burst (fp16 runs at the bf16 rate)",
                          "issued_units_128x128x16_per_tile": tz_units_per_tile(m),
                          "useful_tflop_s": round(useful / (t_tc * 1e-3) / 1e12, 1),
-                         "frac_useful": round(useful / (t_tc * 1e-3) / 1e12 / tc_peak, 4)},
+                         "frac_useful": round(useful / (t_tc * 1e-3) / 1e12 / tc_peak, 4),
+                         **_tc_shape(pk, m, tflops)},
             "int32_roofline": _int_roofline(n * m * m, t_sh, pk), "cpu_baseline": cpu}
 
 

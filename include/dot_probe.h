@@ -23,9 +23,23 @@
  *   DOTP_MUL_LO       mul.lo.u32 alone; unit: one 32-bit multiply;
  *   DOTP_EMPTY        an empty kernel (the launch floor); unit: one launch.
  *
+ * and one tensor-pipe pattern per product shape of the fixed-operand
+ * multiply (Sec. 3.2's column sums as a Toeplitz matrix product): one thread
+ * per CTA issues `iters` x 4 tcgen05.mma of M = 128, N, K = 16 (fp16 digits,
+ * fp32 accumulation) back to back into one accumulator, one CTA per SM (it
+ * holds all of tensor memory; `threads` >= 32 only fills shared memory);
+ * unit: one flop (2 M N K per instruction):
+ *
+ *   DOTP_MMA_N128_TMEM  N = 128, A read from tensor memory (the product of
+ *                       the one-slice kernel, up to 64 limbs);
+ *   DOTP_MMA_N128_SMEM  N = 128, A read from shared memory (two slices);
+ *   DOTP_MMA_N256_TMEM  N = 256, A from tensor memory: the widest single-CTA
+ *                       form.
+ *
  * Memory: the probe allocates its own small output buffer for the duration of
  * the call.  Every call is synchronous.  Errors: a nonzero return is the
- * cudaError_t of the failing CUDA call; 1000 means a bad argument.
+ * cudaError_t of the failing CUDA call; 1000 means a bad argument, 1001 that a
+ * tensor-pipe probe's wait for its products ran out (no timing).
  */
 #ifndef DOT_PROBE_H
 #define DOT_PROBE_H
@@ -47,7 +61,10 @@ enum {
     DOTP_COLSUM_R8 = 1,
     DOTP_MADWIDE_R8 = 2,
     DOTP_MUL_LO = 3,
-    DOTP_EMPTY = 4
+    DOTP_EMPTY = 4,
+    DOTP_MMA_N128_TMEM = 5,
+    DOTP_MMA_N128_SMEM = 6,
+    DOTP_MMA_N256_TMEM = 7
 };
 
 /* Run probe `kind` on the current device: `blocks` thread blocks of `threads`

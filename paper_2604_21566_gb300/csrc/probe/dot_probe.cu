@@ -112,6 +112,86 @@ __global__ void probe_madwide(uint32_t seed, int iters, uint32_t *out)
 
 __global__ void probe_empty() {}
 
+// ------------------------------------------------------------ tensor pipe
+// One thread per CTA issues iters x 4 tcgen05.mma of M = 128, N, K = 16 (fp16
+// in, fp32 accumulate) into one tensor-memory accumulator, A from shared or
+// tensor memory, B from shared memory (128-byte swizzled, K-major, ones and
+// zeros), then commits and waits (bounded) for them.  One CTA per SM (it
+// takes all 512 tensor-memory columns).  out[block] = 1 if the wait ran out.
+#define PROBE_MMA_SMEM (16384 + 32768 + 1024 + 64)
+
+__device__ __forceinline__ uint32_t probe_su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t probe_desc_sw128(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+template <int N, bool ATM>
+__global__ void __launch_bounds__(1024, 1) probe_mma(int iters, uint32_t *out)
+{
+    extern __shared__ __align__(1024) unsigned char probe_sm[];
+    unsigned char *base = probe_sm + ((1024u - (probe_su32(probe_sm) & 1023u)) & 1023u);
+    unsigned char *sA = base, *sB = base + 16384;   // A: 128 x 64 fp16, B: 256 x 64 fp16
+    uint64_t *bar = (uint64_t *)(base + 49152);
+    uint32_t *slot = (uint32_t *)(bar + 1);
+    for (int i = threadIdx.x; i < 49152 / 16; i += blockDim.x)
+        reinterpret_cast<uint4 *>(base)[i] = make_uint4(0x3C003C00u, 0u, 0u, 0u);
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" :: "r"(probe_su32(slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(probe_su32(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *slot;
+    if (threadIdx.x == 0) {
+        // D fp32, A and B fp16, K-major, M = 128, N
+        const uint32_t idesc = (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+        const uint64_t ad = probe_desc_sw128(probe_su32(sA)), bd = probe_desc_sw128(probe_su32(sB));
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int st = 0; st < 4; ++st) {
+                const uint64_t b = bd + (uint64_t)((st * 32) >> 4);
+                if (ATM)
+                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
+                                 :: "r"(tmem), "r"(tmem + 256 + 8 * st), "l"(b), "r"(idesc), "r"(1) : "memory");
+                else
+                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                                 :: "r"(tmem), "l"(ad + (uint64_t)((st * 32) >> 4)), "l"(b), "r"(idesc), "r"(1)
+                                 : "memory");
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     :: "r"(probe_su32(bar)) : "memory");
+        uint32_t done = 0;
+        for (long k = 0; k < (1L << 28) && !done; ++k)
+            asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+                         "selp.u32 %0, 1, 0, p;\n\t}"
+                         : "=r"(done) : "r"(probe_su32(bar)) : "memory");
+        out[blockIdx.x] = done ? 0u : 1u;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(tmem) : "memory");
+}
+
+static bool probe_is_mma(int kind) { return kind >= DOTP_MMA_N128_TMEM && kind <= DOTP_MMA_N256_TMEM; }
+static int probe_mma_n(int kind) { return kind == DOTP_MMA_N256_TMEM ? 256 : 128; }
+
 static const void *probe_fn(int kind)
 {
     switch (kind) {
@@ -120,6 +200,9 @@ static const void *probe_fn(int kind)
     case DOTP_MADWIDE_R8: return (const void *)probe_madwide;
     case DOTP_MUL_LO: return (const void *)probe_mul_lo;
     case DOTP_EMPTY: return (const void *)probe_empty;
+    case DOTP_MMA_N128_TMEM: return (const void *)probe_mma<128, true>;
+    case DOTP_MMA_N128_SMEM: return (const void *)probe_mma<128, false>;
+    case DOTP_MMA_N256_TMEM: return (const void *)probe_mma<256, true>;
     }
     return nullptr;
 }
@@ -132,6 +215,9 @@ static cudaError_t probe_launch(int kind, int blocks, int threads, int iters, ui
     case DOTP_COLSUM_R8: probe_colsum<<<blocks, threads, 0, st>>>(seed, iters, out); break;
     case DOTP_MADWIDE_R8: probe_madwide<<<blocks, threads, 0, st>>>(seed, iters, out); break;
     case DOTP_MUL_LO: probe_mul_lo<<<blocks, threads, 0, st>>>(seed, iters, out); break;
+    case DOTP_MMA_N128_TMEM: probe_mma<128, true><<<blocks, threads, PROBE_MMA_SMEM, st>>>(iters, out); break;
+    case DOTP_MMA_N128_SMEM: probe_mma<128, false><<<blocks, threads, PROBE_MMA_SMEM, st>>>(iters, out); break;
+    case DOTP_MMA_N256_TMEM: probe_mma<256, true><<<blocks, threads, PROBE_MMA_SMEM, st>>>(iters, out); break;
     default: probe_empty<<<blocks, threads, 0, st>>>(); break;
     }
     return cudaGetLastError();
@@ -146,7 +232,8 @@ DOTP_API int dotp_occupancy(int kind, int threads, int *sms, int *blocks_per_sm)
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, threads, 0);
+    if (e == cudaSuccess && probe_is_mma(kind)) *blocks_per_sm = 1;   // all of tensor memory per CTA
+    else if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, threads, 0);
     return (int)e;
 }
 
@@ -158,7 +245,13 @@ DOTP_API int dotp_run(int kind, int blocks, int threads, int iters, int reps, fl
     const double per_thread = kind == DOTP_MUL_PAIR || kind == DOTP_MUL_LO ? (double)iters * PROBE_CHAINS
                             : kind == DOTP_EMPTY ? 0.0
                                                  : (double)iters * PROBE_R * PROBE_R;
-    *units = kind == DOTP_EMPTY ? 1.0 : per_thread * blocks * threads;
+    *units = kind == DOTP_EMPTY ? 1.0
+           : probe_is_mma(kind) ? 2.0 * 128 * probe_mma_n(kind) * 16 * 4 * (double)iters * blocks
+                                : per_thread * blocks * threads;
+    if (probe_is_mma(kind) &&
+        cudaFuncSetAttribute(probe_fn(kind), cudaFuncAttributeMaxDynamicSharedMemorySize, PROBE_MMA_SMEM) !=
+            cudaSuccess)
+        return (int)cudaGetLastError();
     uint32_t *out = nullptr;
     cudaStream_t st = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -175,6 +268,21 @@ DOTP_API int dotp_run(int kind, int blocks, int threads, int iters, int reps, fl
     if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
     *ms = t / (float)reps;
     if (st) cudaStreamSynchronize(st);
+    if (e == cudaSuccess && probe_is_mma(kind)) {   // a wait that ran out voids the timing
+        uint32_t flags[1024];
+        for (int b0 = 0; b0 < blocks && e == cudaSuccess; b0 += 1024) {
+            const int nb = blocks - b0 < 1024 ? blocks - b0 : 1024;
+            e = cudaMemcpy(flags, out + b0, (size_t)nb * 4, cudaMemcpyDeviceToHost);
+            for (int k = 0; k < nb && e == cudaSuccess; ++k)
+                if (flags[k]) {
+                    if (st) cudaStreamDestroy(st);
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    cudaFree(out);
+                    return 1001;
+                }
+        }
+    }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (st) cudaStreamDestroy(st);

@@ -1,5 +1,6 @@
 """Binding of libdotprobe (include/dot_probe.h): the microbenchmarks that give
-the integer-pipe peaks the multiply kernels are reported against.
+the integer-pipe peaks the multiply kernels are reported against, and the
+tensor-pipe rate of each product shape the fixed-operand multiply issues.
 
 ``measure()`` runs each probe over the whole GPU (every SM at its full
 resident occupancy) for a few tens of milliseconds per launch and returns
@@ -13,7 +14,7 @@ import os
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libdotprobe.so")
 
-MUL_PAIR, COLSUM_R8, MADWIDE_R8, MUL_LO, EMPTY = range(5)
+MUL_PAIR, COLSUM_R8, MADWIDE_R8, MUL_LO, EMPTY, MMA_N128_TMEM, MMA_N128_SMEM, MMA_N256_TMEM = range(8)
 THREADS = 256
 
 _lib = None
@@ -58,7 +59,10 @@ def measure(target_ms: float = 25.0, reps: int = 5):
     names = {MUL_PAIR: ("mul_pair", "limb product (mul.lo + mul.hi pair)"),
              COLSUM_R8: ("colsum_r8", "limb product (multiply pair + 3-word add chain)"),
              MADWIDE_R8: ("madwide_r8", "digit product (mad.wide.u32 into 64 bits)"),
-             MUL_LO: ("mul_lo", "32-bit multiply (mul.lo.u32)")}
+             MUL_LO: ("mul_lo", "32-bit multiply (mul.lo.u32)"),
+             MMA_N128_TMEM: ("mma_n128_tmem", "flop (tcgen05.mma M=128 N=128 K=16, A in tensor memory)"),
+             MMA_N128_SMEM: ("mma_n128_smem", "flop (tcgen05.mma M=128 N=128 K=16, A in shared memory)"),
+             MMA_N256_TMEM: ("mma_n256_tmem", "flop (tcgen05.mma M=128 N=256 K=16, A in tensor memory)")}
     out = {}
     for kind, (name, unit) in names.items():
         sms, per = occupancy(kind)
