@@ -100,23 +100,25 @@ def algorithmic_bytes(m: int, batch: int) -> int:
 
 
 def read_traffic():
-    """dram bytes per launch of the dominant kernel from the committed ncu
-    summary, or None if missing or taken on different kernel sources."""
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary: (read + write, read, write), or Nones if the summary is missing
+    or was taken on different kernel sources."""
     try:
         text = open(PROFILE).read()
     except OSError:
-        return None
+        return None, None, None
     vals = {}
     for ln in text.splitlines():
         if ":" in ln and ln.strip().startswith("- "):
             k, v = ln.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
     if vals.get("kernel_source_hash") != kernel_source_hash():
-        return None
+        return None, None, None
     try:
-        return int(vals["dram_bytes_per_launch"])
+        rd, wr = int(vals["dram_read_bytes_per_launch"]), int(vals["dram_write_bytes_per_launch"])
     except (KeyError, ValueError):
-        return None
+        return None, None, None
+    return rd + wr, rd, wr
 
 
 def peaks():
@@ -318,6 +320,7 @@ def gpu_arm(args, rank, world, local):
         dom_ms = 0.5 * (per_launch["add_short"] + per_launch["sub_short"])
         x, _ = data[dom]
         alg = algorithmic_bytes(x.shape[1], x.shape[0])
+        traffic, traffic_rd, traffic_wr = read_traffic()
         achieved = alg / (dom_ms * 1e-3) / 1e9
         parts_out = {}
         for name in per_launch:
@@ -344,7 +347,13 @@ def gpu_arm(args, rank, world, local):
             "roofline": {"bound": "hbm", "kernel": "addsub_warp_kernel (4096-bit ops)",
                          "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(achieved / hbm, 4), "peak_source": src,
-                         "traffic": read_traffic(), "algorithmic_bytes_per_launch": alg},
+                         "traffic": traffic, "traffic_read": traffic_rd, "traffic_write": traffic_wr,
+                         "traffic_source": "ncu dram__bytes_read.sum / dram__bytes_write.sum of one "
+                                           "launch that follows an identical launch (its writes include "
+                                           "the evictions of the previous launch's dirty lines), "
+                                           "scaled from 2^18 to the bench's 2^20 pairs",
+                         "algorithmic_bytes_per_launch": alg,
+                         "algorithmic_read_bytes_per_launch": x.shape[0] * 8 * x.shape[1]},
             "parts": parts_out,
             "cpu_baseline": cpu,
             "e2e": {"value": round(job_throughput(ops_step, world, e2e_ms), 4), "unit": "Gop/s",
@@ -388,8 +397,10 @@ def reference_arm(args, rank, world):
         return
     from paper_2604_21566_gb300 import workloads as W
     import oracle
-    # each step: a bounded row sample of both parts, add and sub
-    data = W.addsub_bandwidth(short_batch=1 << 17, long_batch=8)
+    # each step: one whole step of the workload (add and sub of both parts),
+    # the same rows and calls as the GPU arm's cpu_baseline; about 30 ms on 16
+    # host cores
+    data = W.addsub_bandwidth()
     cores = oracle.cores()
     names = ("add_short", "add_long", "sub_short", "sub_long")
 
@@ -409,7 +420,7 @@ def reference_arm(args, rank, world):
         ops += step()
     dt = time.perf_counter() - t0
     value = ops / dt / 1e9
-    sample = "per step: 2^17 x 4096-bit + 8 x 2^22-bit pairs, add and sub (a row sample of the workload)"
+    sample = "per step: the whole workload (2^20 x 4096-bit + 64 x 2^22-bit pairs, add and sub)"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "Gop/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -430,14 +441,17 @@ def profile_case(args):
             the bench's own part, at the bench's grid);
     mul  -- dot_mul on 2^16 pairs of 8192-bit operands (256 MB in + out);
     shared -- dot_mul_shared on the tensor cores, 2^16 x 2048-bit (50 MB);
+    shared2p18 -- the same on 2^18 operands (201 MB, > L2, so that the DRAM
+            counters see the products written);
     shared128 -- the same at 4096 bits (two K slices, 100 MB)."""
     import torch
     from paper_2604_21566_gb300 import dot
     from paper_2604_21566_gb300 import workloads as W
     torch.cuda.set_device(0)
     ctx = dot.Context(0)
-    if args.case in ("shared", "shared128"):
-        f, bb = W.shared_operand(m=128 if args.case == "shared128" else 64)
+    if args.case in ("shared", "shared2p18", "shared128"):
+        f, bb = W.shared_operand(m=128 if args.case == "shared128" else 64,
+                                 batch=1 << (18 if args.case == "shared2p18" else 16))
         fd = torch.from_numpy(f.view(np.int32)).cuda()
         b = torch.from_numpy(bb.view(np.int32)).cuda()
         p = torch.empty((bb.shape[0], 2 * bb.shape[1]), dtype=torch.int32, device="cuda")
@@ -963,7 +977,7 @@ def main():
                     help="run only the small ncu case of the dominant kernel")
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--only", default="", help="--suite rows to run: mix,mul,mixed,shared,splitk,unsat,mulx,sqr,kara")
-    ap.add_argument("--case", choices=["add", "long", "mul", "shared", "shared128"], default="add",
+    ap.add_argument("--case", choices=["add", "long", "mul", "shared", "shared2p18", "shared128"], default="add",
                     help="which kernel --profile-case runs")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
