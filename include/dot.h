@@ -337,7 +337,8 @@ DOT_API dot_status_t dot_add_noalloc(int device, const uint32_t *a, const uint32
 typedef struct dot_plan {
     int kernel;          /* 1 warp-segmented add/sub, 2 tiled add/sub with
                             look-back, 3 column-sum multiply, 4 one product
-                            per thread (m <= 16), 0 nothing to do */
+                            per thread (m <= 16, or m <= 32 in batches of
+                            at least 16384), 0 nothing to do */
     int seg_limbs;       /* limbs per thread segment (vector width)          */
     int lanes_per_op;    /* threads that cooperate on one op (<= 32), or the
                             threads of one tile for kernel 2                  */

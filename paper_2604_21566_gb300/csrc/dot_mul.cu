@@ -188,17 +188,94 @@ mul_thread_kernel(const uint32_t *a, const uint32_t *b, uint32_t *p, int m, size
     }
 }
 
+// Products of 17..32 limbs, one per thread, for batches that give every SM
+// many threads: the operands stay in registers, each column is summed in four
+// interleaved chains (rows i mod 4, so that consecutive products do not wait
+// on one carry chain), and the result leaves four limbs at a time as the
+// columns complete instead of being held whole.  Blocks of 64 threads spread
+// a batch of 2^16 over the SMs within one block of the mean (256-thread
+// blocks left some SMs twice the work of others).
+#define MUL_THREAD_WIDE_THREADS 64
+template <int M>
+__global__ void __launch_bounds__(MUL_THREAD_WIDE_THREADS)
+mul_thread_wide_kernel(const uint32_t *a, const uint32_t *b, uint32_t *p, int m, size_t batch, int vec_in,
+                       int vec_out)
+{
+    static_assert(M % 4 == 0, "columns leave in groups of four");
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t op = (size_t)blockIdx.x * blockDim.x + threadIdx.x; op < batch; op += stride) {
+        uint32_t x[M], y[M];
+        const uint32_t *ar = a + op * (size_t)m, *br = b + op * (size_t)m;
+        if (vec_in) {   // m % 4 == 0 and 16-byte aligned rows
+#pragma unroll
+            for (int q = 0; q < M / 4; ++q) {
+                uint4 u = make_uint4(0u, 0u, 0u, 0u), v = u;
+                if (4 * q < m) {
+                    u = ld_stream4(ar + 4 * q);
+                    v = ld_stream4(br + 4 * q);
+                }
+                x[4 * q] = u.x; x[4 * q + 1] = u.y; x[4 * q + 2] = u.z; x[4 * q + 3] = u.w;
+                y[4 * q] = v.x; y[4 * q + 1] = v.y; y[4 * q + 2] = v.z; y[4 * q + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+                x[i] = i < m ? ld_stream1(ar + i) : 0u;
+                y[i] = i < m ? ld_stream1(br + i) : 0u;
+            }
+        }
+        uint32_t *pr = p + op * 2 * (size_t)m;
+        uint32_t ob[4];
+        uint32_t c0 = 0, c1 = 0, c2 = 0;   // carry into the column, three words
+#pragma unroll
+        for (int c = 0; c < 2 * M; ++c) {
+            if (c < 2 * M - 1) {
+                uint32_t e[4][3];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) e[q][0] = e[q][1] = e[q][2] = 0u;
+#pragma unroll
+                for (int i = (c - M + 1 > 0 ? c - M + 1 : 0); i <= (c < M - 1 ? c : M - 1); ++i)
+                    mac1(e[i & 3][0], e[i & 3][1], e[i & 3][2], x[i], y[c - i]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) add3w(c0, c1, c2, e[q][0], e[q][1], e[q][2]);
+                ob[c & 3] = c0;
+                c0 = c1;
+                c1 = c2;
+                c2 = 0;
+            } else {
+                ob[c & 3] = c0;
+            }
+            if ((c & 3) == 3) {   // limbs c - 3 .. c are final
+                const int c4 = c - 3;
+                if (vec_out) {    // 2m % 4 == 0: a group is wholly inside the row or past it
+                    if (c4 < 2 * m) st_stream4(pr + c4, make_uint4(ob[0], ob[1], ob[2], ob[3]));
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (c4 + k < 2 * m) st_stream1(pr + c4 + k, ob[k]);
+                }
+            }
+        }
+    }
+}
+
 template <int M>
 static dot_status_t launch_mul_thread(dot_ctx_t ctx, const uint32_t *a, const uint32_t *b, uint32_t *p, size_t m,
                                       size_t batch, cudaStream_t st)
 {
-    const void *fn = (const void *)mul_thread_kernel<M>;
+    const void *fn;
+    if constexpr (M > DOT_MUL_THREAD_MAX) fn = (const void *)mul_thread_wide_kernel<M>;
+    else fn = (const void *)mul_thread_kernel<M>;
     const bool vec_in = (m % 4 == 0) && aligned16(a) && aligned16(b);
     const bool vec_out = (m % 2 == 0) && aligned16(p);
-    const size_t need = dot_ceil_div(batch, (size_t)256);
-    const size_t cap = (size_t)ctx->num_sms * dot_blocks_per_sm(fn, 256, 0);
+    const int bs = M > DOT_MUL_THREAD_MAX ? MUL_THREAD_WIDE_THREADS : 256;
+    const size_t need = dot_ceil_div(batch, (size_t)bs);
+    const size_t cap = (size_t)ctx->num_sms * dot_blocks_per_sm(fn, bs, 0);
     const unsigned grid = (unsigned)(need < cap ? need : cap);
-    mul_thread_kernel<M><<<grid, 256, 0, st>>>(a, b, p, (int)m, batch, vec_in, vec_out);
+    if constexpr (M > DOT_MUL_THREAD_MAX)
+        mul_thread_wide_kernel<M><<<grid, MUL_THREAD_WIDE_THREADS, 0, st>>>(a, b, p, (int)m, batch, vec_in, vec_out);
+    else
+        mul_thread_kernel<M><<<grid, 256, 0, st>>>(a, b, p, (int)m, batch, vec_in, vec_out);
     return cudaGetLastError() == cudaSuccess ? DOT_OK : DOT_ECUDA;
 }
 
@@ -209,7 +286,9 @@ static dot_status_t launch_mul_thread_any(dot_ctx_t ctx, const uint32_t *a, cons
     if (m <= 4) return launch_mul_thread<4>(ctx, a, b, p, m, batch, st);
     if (m <= 8) return launch_mul_thread<8>(ctx, a, b, p, m, batch, st);
     if (m <= 12) return launch_mul_thread<12>(ctx, a, b, p, m, batch, st);
-    return launch_mul_thread<16>(ctx, a, b, p, m, batch, st);
+    if (m <= 16) return launch_mul_thread<16>(ctx, a, b, p, m, batch, st);
+    if (m <= 24) return launch_mul_thread<24>(ctx, a, b, p, m, batch, st);
+    return launch_mul_thread<32>(ctx, a, b, p, m, batch, st);
 }
 
 // ------------------------------------------------------------- launchers

@@ -17,6 +17,10 @@ enum {
 };
 // largest operand (limbs) of the one-product-per-thread multiply
 #define DOT_MUL_THREAD_MAX 16
+// up to 32 limbs one product per thread too, when the batch gives every SM
+// many threads (smaller batches spread an op over several lanes instead)
+#define DOT_MUL_THREAD_WIDE_MAX 32
+#define DOT_MUL_THREAD_WIDE_MIN_BATCH 16384
 
 #define DOT_TILE_THREADS 256
 #define DOT_WARP_MAX_CHUNKS 4
@@ -85,7 +89,9 @@ static inline dot_status_t dot_make_plan(int op, size_t m, size_t batch, bool ve
     if (op == DOT_OP_MUL) {
         if (m == 0) return DOT_OK;
         if (m > DOT_MUL_MAX_LIMBS) return DOT_EUNSUPPORTED;
-        if (m <= DOT_MUL_THREAD_MAX && !(knob && dot_knob_valid(op, m, knob))) {
+        const bool by_thread = m <= DOT_MUL_THREAD_MAX ||
+                               (m <= DOT_MUL_THREAD_WIDE_MAX && batch >= DOT_MUL_THREAD_WIDE_MIN_BATCH);
+        if (by_thread && !(knob && dot_knob_valid(op, m, knob))) {
             // small operands: one product per thread (a tuned column shape
             // selects the column-sum kernel instead)
             pl->kernel = DOT_K_MUL_THREAD;

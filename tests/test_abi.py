@@ -86,6 +86,11 @@ def test_mul_columns_fill_the_warp():
     with pytest.raises(dot.DotError):
         dot.plan(7, 4, 1)
     assert dot.plan(dot.OP_ADD, 4, 0).kernel == 0
+    # 17..32 limbs: one product per thread only for batches of at least 2^14
+    assert (dot.plan(dot.OP_MUL, 32, 1 << 16).kernel, dot.plan(dot.OP_MUL, 32, 1 << 16).seg_limbs) == (4, 32)
+    assert dot.plan(dot.OP_MUL, 17, 1 << 14).kernel == 4
+    assert dot.plan(dot.OP_MUL, 32, 4096).kernel == 3
+    assert dot.plan(dot.OP_MUL, 33, 1 << 16).kernel == 3
 
 
 def test_probe_library_exports():

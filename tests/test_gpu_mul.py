@@ -41,6 +41,35 @@ def test_sizes_and_classes(D, m):
         assert_same(run(D, x, y), oracle.mul(x, y), f"mul m={m} {cls}")
 
 
+@pytest.mark.parametrize("m", [17, 20, 23, 24, 25, 28, 31, 32])
+def test_one_product_per_thread_wide(D, m):
+    """17..32 limbs in batches of at least 2^14 take one product per thread:
+    every class, a ragged last block, and the scalar path of odd m."""
+    assert D.plan(D.OP_MUL, m, (1 << 14) + 37).kernel == 4
+    g = W.rng(2600 + m)
+    for cls in W.CLASSES:
+        x, y = W.class_operands(g, cls, (1 << 14) + 37, m)
+        assert_same(run(D, x, y), oracle.mul(x, y, threads=8), f"m={m} {cls}")
+
+
+def test_one_product_per_thread_unaligned(D):
+    """The wide per-thread product on rows that are not 16-byte aligned (scalar
+    loads and stores), with guard limbs around the output."""
+    import torch
+    m, n = 32, (1 << 14) + 5
+    g = W.rng(2700)
+    x, y = W.uniform_limbs(g, (n, m)), W.uniform_limbs(g, (n, m))
+    xa = torch.zeros(n * m + 1, dtype=torch.int32, device="cuda")
+    xa[1:] = dev(x).reshape(-1)
+    out = torch.full((n * 2 * m + 2,), 0x5A5A5A5A, dtype=torch.int32, device="cuda")
+    view = out[1:1 + n * 2 * m].view(n, 2 * m)
+    D.mul(xa[1:].view(n, m), dev(y), view)
+    torch.cuda.synchronize()
+    h = host(out)
+    assert h[0] == 0x5A5A5A5A and h[-1] == 0x5A5A5A5A
+    assert_same(h[1:1 + n * 2 * m].reshape(n, 2 * m), oracle.mul(x, y, threads=8), "unaligned")
+
+
 def test_closed_form_all_ones(D):
     """(2^n - 1)^2 = 2^{2n} - 2^{n+1} + 1 for every supported size class."""
     for m in (1, 4, 8, 16, 17, 32, 256, 257, 512):
