@@ -77,6 +77,20 @@ def test_full_length_ripple_across_tiles(D, op):
     assert_same(c, wc, op + " carry")
 
 
+@pytest.mark.parametrize("op", ["add", "sub"])
+def test_long_operands_80_pairs(D, op):
+    """80 pairs of 2^22-bit operands (84 MB of operands, 2560 tiles: more
+    than one round of resident blocks, and a last round that not every block
+    works on), with propagate runs crossing tiles and a full-length ripple
+    row."""
+    d = W.addsub_bandwidth(short_batch=0, long_batch=80)
+    x, y = d[f"{op}_long"]
+    s, c = run(D, op, x, y)
+    ws, wc = want(op, x, y, threads=16)
+    assert_same(s, ws, f"{op} long")
+    assert_same(c, wc, f"{op} long carry")
+
+
 def test_correctness_mix(D):
     d = W.correctness_mix()
     for op, (x, y) in (("add", (d["x"], d["y"])), ("sub", (d["a_sub"], d["b_sub"]))):
