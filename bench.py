@@ -443,12 +443,27 @@ def profile_case(args):
     shared -- dot_mul_shared on the tensor cores, 2^16 x 2048-bit (50 MB);
     shared2p18 -- the same on 2^18 operands (201 MB, > L2, so that the DRAM
             counters see the products written);
-    shared128 -- the same at 4096 bits (two K slices, 100 MB)."""
+    shared128 -- the same at 4096 bits (two K slices, 100 MB);
+    mixed -- dot_mixed_ragged on 20k ops of the mixed-batch recipe (graph
+            replay: classify, plan, scatter, then the product and add/sub
+            kernels)."""
     import torch
     from paper_2604_21566_gb300 import dot
     from paper_2604_21566_gb300 import workloads as W
     torch.cuda.set_device(0)
     ctx = dot.Context(0)
+    if args.case == "mixed":
+        w = W.ragged_mixed(nops=20_000)
+        ddesc = torch.from_numpy(ragged_descriptors(w).view(np.uint8).copy()).cuda()
+        a, b = _dv(w["a"]), _dv(w["b"])
+        r = torch.zeros(int(w["r_off"][-1]), dtype=torch.int32, device="cuda")
+        cr = torch.zeros(w["op"].size, dtype=torch.int32, device="cuda")
+        for _ in range(args.launches):
+            dot.mixed_ragged(ddesc, a, b, r, cr, ctx=ctx)
+        torch.cuda.synchronize()
+        assert ctx.check() == dot.OK
+        print("profile case done")
+        return
     if args.case in ("shared", "shared2p18", "shared128"):
         f, bb = W.shared_operand(m=128 if args.case == "shared128" else 64,
                                  batch=1 << (18 if args.case == "shared2p18" else 16))
@@ -977,7 +992,8 @@ def main():
                     help="run only the small ncu case of the dominant kernel")
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--only", default="", help="--suite rows to run: mix,mul,mixed,shared,splitk,unsat,mulx,sqr,kara")
-    ap.add_argument("--case", choices=["add", "long", "mul", "shared", "shared2p18", "shared128"], default="add",
+    ap.add_argument("--case", choices=["add", "long", "mul", "shared", "shared2p18", "shared128", "mixed"],
+                    default="add",
                     help="which kernel --profile-case runs")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)

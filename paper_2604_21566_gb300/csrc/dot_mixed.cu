@@ -11,17 +11,21 @@
 //      over the two add/sub buckets, 64 warps per SM so that enough of them
 //      have loads in flight (as one item each behind the products, claimed
 //      one at a time, they ran at a seventh of the memory bandwidth);
-//   5. run: one persistent kernel for the products; each warp takes work
-//      items from a global counter, heaviest buckets first
-//      (longest-processing-time order), and runs the multiply (column-block
-//      sums, Alg. 2) for the item's ops.  Small multiplies share a warp: a bucket fixes the
+//   5. run: two persistent kernels for the products, one for the
+//      257..512-limb buckets and one for the rest (so that the smaller
+//      shapes are not held to the registers, and the occupancy, of the
+//      largest); each warp takes work items from its kernel's counter,
+//      heaviest buckets first (longest-processing-time order), and runs the
+//      multiply (column-block sums, Alg. 2) for the item's ops.  Small multiplies share a warp: a bucket fixes the
 //      run width T, and each op of the item takes a run of T lanes.  A bucket
 //      also fixes the columns per lane R, chosen so that an op's ceil(m / R)
 //      lanes fill most of its run: the 257..512-limb range is split at 384
 //      into R = 12 and R = 16 (with R = 16 alone a log-uniform size mix
 //      leaves 28% of those lanes idle, with the split about 15%).
-// The five launches are captured once into a CUDA graph per context; later
-// calls only update the graph's kernel-node parameters and replay it.
+// The six launches are captured once into a CUDA graph per context (the
+// add/sub kernel and the smaller products on one branch, the largest
+// products on another); later calls only update the graph's kernel-node
+// parameters and replay it.
 #include <stdlib.h>
 #include <string.h>
 
@@ -34,7 +38,7 @@
 // bucket ids, in processing order
 enum { BK_M16 = 0, BK_M12, BK_M8C, BK_M8B, BK_M8A, BK_M4, BK_ASL, BK_ASS, NBK };
 #define MIX_WARPS 4
-#define MIX_REGION_WORDS 1056   // largest per-warp staging: 2 * 512 + 2 * 16 words
+__host__ __device__ constexpr int cmax(int x, int y) { return x > y ? x : y; }
 #define MIX_MAX_OPS (1ull << 28)
 
 struct MixedMeta {
@@ -43,8 +47,8 @@ struct MixedMeta {
     uint32_t base[NBK];    // first slot of each bucket in `order`
     uint32_t item_base[NBK + 1];
     uint32_t pad;
-    unsigned long long next_item;
-    unsigned long long done;
+    unsigned long long next_item[2];   // work counters of the two product kernels
+    unsigned long long done[2];
 };
 
 struct MixedScratch {
@@ -54,8 +58,8 @@ struct MixedScratch {
     size_t cap;
     cudaGraphExec_t exec;
     cudaGraph_t graph;
-    cudaGraphNode_t node[5];
-    int persist_blocks;
+    cudaGraphNode_t node[6];
+    int persist_blocks, narrow_blocks;
     int as_blocks;
     cudaEvent_t fork, join;
 };
@@ -140,15 +144,19 @@ mixed_scatter(const uint32_t *slot, size_t nops, const MixedMeta *meta, uint32_t
     order[meta->base[s >> 28] + (s & 0x0fffffffu)] = (uint32_t)i;
 }
 
-// the ops of one multiply work item: run grp of the warp takes op k0 + grp
-template <int R, int T>
+// staging words one warp needs for shape (R, T): 32 / T ops, each with its A
+// row, its B row and the B pads
+__host__ __device__ constexpr int mix_region_words(int R, int T) { return (32 / T) * (2 * T * R + 2 * R); }
+
+// the ops of one multiply work item: run grp of the warp takes op k0 + grp;
+// RW: the staging words the caller gives each warp
+template <int R, int T, int RW>
 __device__ __forceinline__ void mixed_mul_item(const dot_desc_t *desc, const uint32_t *order, uint32_t base,
                                                uint32_t n, uint32_t k0, const uint32_t *a, const uint32_t *b,
                                                uint32_t *r, uint32_t *carry, uint32_t *wsmem)
 {
-    constexpr int OPI = 32 / T;
     constexpr int REGION = 2 * T * R + 2 * R;
-    static_assert(OPI * REGION <= MIX_REGION_WORDS, "staging region");
+    static_assert(mix_region_words(R, T) <= RW, "staging region");
     const int lane = (int)lane_id();
     const int grp = lane / T, t = lane - grp * T;
     const uint32_t idx = k0 + grp;
@@ -221,45 +229,60 @@ mixed_addsub(const dot_desc_t *desc, const uint32_t *order, const MixedMeta *met
     }
 }
 
+// The products in two persistent kernels, each over a range of buckets
+// [LO, HI) with a work counter of its own: the 257..512-limb buckets (R = 16
+// and 12, the most registers) and the rest (R <= 8), so that the smaller
+// shapes run at the occupancy their registers allow instead of the largest
+// shape's.
+template <int LO, int HI, int K>
 __global__ void __launch_bounds__(MIX_WARPS * 32)
 mixed_run(const dot_desc_t *desc, const uint32_t *order, MixedMeta *meta, const uint32_t *a,
           const uint32_t *b, uint32_t *r, uint32_t *carry)
 {
-    __shared__ __align__(16) uint32_t smem[MIX_WARPS * MIX_REGION_WORDS];
+    // per-warp staging words: the largest shape of the kernel's buckets
+    constexpr int RW = LO == BK_M16 ? mix_region_words(16, 32)
+                                    : cmax(cmax(mix_region_words(8, 32), mix_region_words(8, 16)),
+                                           cmax(mix_region_words(8, 8), mix_region_words(4, 4)));
+    __shared__ __align__(16) uint32_t smem[MIX_WARPS * RW];
     const int lane = (int)lane_id(), warp = (int)(threadIdx.x >> 5);
-    uint32_t *wsmem = smem + warp * MIX_REGION_WORDS;
-    const uint32_t total = meta->item_base[BK_ASL];   // the product buckets come first
+    uint32_t *wsmem = smem + warp * RW;
+    const uint32_t first = meta->item_base[LO], total = meta->item_base[HI];
     for (;;) {
         unsigned long long item = 0;
-        if (lane == 0) item = atomicAdd(&meta->next_item, 1ull);
+        if (lane == 0) item = first + atomicAdd(&meta->next_item[K], 1ull);
         item = __shfl_sync(DOT_FULL, item, 0);
         if (item >= total) break;
-        int bk = 0;
+        int bk = LO;
 #pragma unroll
-        for (int q = 1; q < NBK; ++q)
+        for (int q = LO + 1; q < HI; ++q)
             if (item >= meta->item_base[q]) bk = q;
         const uint32_t n = meta->n[bk], base = meta->base[bk];
         const uint32_t k0 = (uint32_t)(item - meta->item_base[bk]) * bucket_ops_per_item(bk);
-        switch (bk) {
-        case BK_M16: mixed_mul_item<16, 32>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
-        case BK_M12: mixed_mul_item<12, 32>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
-        case BK_M8C: mixed_mul_item<8, 32>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
-        case BK_M8B: mixed_mul_item<8, 16>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
-        case BK_M8A: mixed_mul_item<8, 8>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
-        default: mixed_mul_item<4, 4>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
+        if constexpr (LO == BK_M16) {
+            if (bk == BK_M16) mixed_mul_item<16, 32, RW>(desc, order, base, n, k0, a, b, r, carry, wsmem);
+            else mixed_mul_item<12, 32, RW>(desc, order, base, n, k0, a, b, r, carry, wsmem);
+        } else {
+            switch (bk) {
+            case BK_M8C: mixed_mul_item<8, 32, RW>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
+            case BK_M8B: mixed_mul_item<8, 16, RW>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
+            case BK_M8A: mixed_mul_item<8, 8, RW>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
+            default: mixed_mul_item<4, 4, RW>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
+            }
         }
     }
     // the last warp out clears the work counter for the next call
     if (lane == 0) {
         __threadfence();
-        const unsigned long long prev = atomicAdd(&meta->done, 1ull);
+        const unsigned long long prev = atomicAdd(&meta->done[K], 1ull);
         if (prev == (unsigned long long)gridDim.x * MIX_WARPS - 1) {
-            meta->next_item = 0;
-            meta->done = 0;
+            meta->next_item[K] = 0;
+            meta->done[K] = 0;
             __threadfence();
         }
     }
 }
+#define MIX_RUN_WIDE mixed_run<BK_M16, BK_M8C, 0>
+#define MIX_RUN_NARROW mixed_run<BK_M8C, BK_ASL, 1>
 
 // ------------------------------------------------------------------ host
 static MixedScratch *g_scratch_of(dot_ctx_t ctx);
@@ -293,7 +316,8 @@ static dot_status_t mixed_prepare(dot_ctx_t ctx, MixedScratch *S, size_t nops)
         // blocks per SM instead of three, to leave the add/sub branch room,
         // the products ran 1.4x slower); the add/sub blocks fill in as the
         // product blocks finish
-        S->persist_blocks = ctx->num_sms * dot_blocks_per_sm((const void *)mixed_run, MIX_WARPS * 32, 0);
+        S->persist_blocks = ctx->num_sms * dot_blocks_per_sm((const void *)MIX_RUN_WIDE, MIX_WARPS * 32, 0);
+        S->narrow_blocks = ctx->num_sms * dot_blocks_per_sm((const void *)MIX_RUN_NARROW, MIX_WARPS * 32, 0);
         S->as_blocks = ctx->num_sms * MIX_AS_BLOCKS_PER_SM;
         if (cudaEventCreateWithFlags(&S->fork, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&S->join, cudaEventDisableTiming) != cudaSuccess)
@@ -317,7 +341,7 @@ static dot_status_t mixed_prepare(dot_ctx_t ctx, MixedScratch *S, size_t nops)
 
 static dot_status_t mixed_capture(dot_ctx_t ctx, MixedScratch *S, const MixedArgs &A)
 {
-    // record the four launches once on a private stream, then keep the graph
+    // record the six launches once on a private stream, then keep the graph
     cudaStream_t cs = ctx->side[0];
     if (cudaStreamSynchronize(cs) != cudaSuccess) return DOT_ECUDA;
     if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return DOT_ECUDA;
@@ -331,27 +355,28 @@ static dot_status_t mixed_capture(dot_ctx_t ctx, MixedScratch *S, const MixedArg
     if (cudaEventRecord(S->fork, cs) != cudaSuccess || cudaStreamWaitEvent(cs2, S->fork, 0) != cudaSuccess)
         return DOT_ECUDA;
     mixed_addsub<<<S->as_blocks, MIX_AS_THREADS, 0, cs2>>>(A.desc, A.order, A.meta, A.a, A.b, A.r, A.carry);
-    mixed_run<<<S->persist_blocks, MIX_WARPS * 32, 0, cs>>>(A.desc, A.order, A.meta, A.a, A.b, A.r, A.carry);
+    MIX_RUN_NARROW<<<S->narrow_blocks, MIX_WARPS * 32, 0, cs2>>>(A.desc, A.order, A.meta, A.a, A.b, A.r, A.carry);
+    MIX_RUN_WIDE<<<S->persist_blocks, MIX_WARPS * 32, 0, cs>>>(A.desc, A.order, A.meta, A.a, A.b, A.r, A.carry);
     if (cudaEventRecord(S->join, cs2) != cudaSuccess || cudaStreamWaitEvent(cs, S->join, 0) != cudaSuccess)
         return DOT_ECUDA;
     cudaGraph_t g = nullptr;
     if (cudaStreamEndCapture(cs, &g) != cudaSuccess || !g) return DOT_ECUDA;
     size_t nn = 0;
     cudaGraphNode_t nodes[8];
-    if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess || nn != 5) {
+    if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess || nn != 6) {
         cudaGraphDestroy(g);
         return DOT_ECUDA;
     }
     cudaGraphGetNodes(g, nodes, &nn);
-    const void *fns[5] = {(const void *)mixed_classify, (const void *)mixed_plan, (const void *)mixed_scatter,
-                          (const void *)mixed_addsub, (const void *)mixed_run};
+    const void *fns[6] = {(const void *)mixed_classify, (const void *)mixed_plan, (const void *)mixed_scatter,
+                          (const void *)mixed_addsub, (const void *)MIX_RUN_WIDE, (const void *)MIX_RUN_NARROW};
     for (size_t i = 0; i < nn; ++i) {
         cudaKernelNodeParams kp;
         if (cudaGraphKernelNodeGetParams(nodes[i], &kp) != cudaSuccess) {
             cudaGraphDestroy(g);
             return DOT_ECUDA;
         }
-        for (int k = 0; k < 5; ++k)
+        for (int k = 0; k < 6; ++k)
             if (kp.func == fns[k]) S->node[k] = nodes[i];
     }
     cudaGraphExec_t ex = nullptr;
@@ -408,13 +433,14 @@ DOT_API dot_status_t dot_mixed_ragged(dot_ctx_t ctx, const dot_desc_t *desc, siz
     void *p0[6], *p1[1], *p2[4], *p3[7];
     fill_params(A, p0, p1, p2, p3);
     const unsigned g1 = (unsigned)((nops + 255) / 256);
-    const void *fns[5] = {(const void *)mixed_classify, (const void *)mixed_plan, (const void *)mixed_scatter,
-                          (const void *)mixed_addsub, (const void *)mixed_run};
-    void **params[5] = {p0, p1, p2, p3, p3};
-    const dim3 grids[5] = {dim3(g1), dim3(1), dim3(g1), dim3((unsigned)S->as_blocks),
-                           dim3((unsigned)S->persist_blocks)};
-    const dim3 blocks[5] = {dim3(256), dim3(32), dim3(256), dim3(MIX_AS_THREADS), dim3(MIX_WARPS * 32)};
-    for (int k = 0; k < 5; ++k) {
+    const void *fns[6] = {(const void *)mixed_classify, (const void *)mixed_plan, (const void *)mixed_scatter,
+                          (const void *)mixed_addsub, (const void *)MIX_RUN_WIDE, (const void *)MIX_RUN_NARROW};
+    void **params[6] = {p0, p1, p2, p3, p3, p3};
+    const dim3 grids[6] = {dim3(g1), dim3(1), dim3(g1), dim3((unsigned)S->as_blocks),
+                           dim3((unsigned)S->persist_blocks), dim3((unsigned)S->narrow_blocks)};
+    const dim3 blocks[6] = {dim3(256), dim3(32), dim3(256), dim3(MIX_AS_THREADS), dim3(MIX_WARPS * 32),
+                            dim3(MIX_WARPS * 32)};
+    for (int k = 0; k < 6; ++k) {
         cudaKernelNodeParams kp;
         memset(&kp, 0, sizeof kp);
         kp.func = (void *)fns[k];
