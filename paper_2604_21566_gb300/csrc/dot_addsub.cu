@@ -267,19 +267,23 @@ addsub_tile_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint32_t *
 }
 
 // ============================ tiled kernel (2b): bulk-copy prefetch + look-back
-// Same tiles and look-back as above, for 16-byte aligned rows with m % 4 == 0,
-// on a static round-robin schedule: block b takes tiles b, b + G, b + 2G, ...
-// (G blocks, all resident: a cooperative launch).  Each block streams its
-// tiles through two shared-memory stages (cp.async.bulk, completion counted on
-// an mbarrier) and works one tile AHEAD: as soon as tile k + 1 has arrived it
-// forms and publishes that tile's aggregate, and only then resolves tile k's
-// carry-in and stores tile k.  A tile's predecessor therefore has almost always
-// published a round earlier, and the look-back wait leaves the critical path;
-// publishing only after the previous tile was stored made every block wait on
-// its predecessor's progress, and the delays travelled along each op's tiles.
-// A tile's predecessor belongs to the previous block in the same round (or to
-// the last block one round earlier); all blocks are resident and publish in
-// ticket order within a block, so the waits always end.
+// Same tiles and look-back as above, for 16-byte aligned rows with m % 4 == 0.
+// A persistent grid (one block per resident slot) takes tiles in ticket order
+// from the atomic counter; each block holds one ticket in reserve, so the
+// atomic's latency is paid while the previous copies are in flight rather
+// than before the next copy can start.  Each block streams its tiles through
+// two shared-memory stages (cp.async.bulk, completion counted on an mbarrier)
+// and works one tile AHEAD: as soon as tile k + 1 has arrived it forms and
+// publishes that tile's aggregate, and only then resolves tile k's carry-in and
+// stores tile k.  A tile's predecessor therefore has almost always published
+// already, and the look-back wait leaves the critical path; publishing only
+// after the previous tile was stored made every block wait on its
+// predecessor's progress, and the delays travelled along each op's tiles.
+// The waits always end: a tile's predecessor has a lower ticket, taken
+// earlier by a block that is running, and a block's tickets increase, so the
+// lowest unfinished ticket never waits on a higher one.  Tickets also spread
+// the tiles by arrival: a block whose copies come back early takes more of
+// them (a static round-robin schedule ended with the slowest block).
 template <bool SUB, int NCH>
 struct TileRegs {
     Segment<SUB, 4> sg[NCH];
@@ -365,8 +369,10 @@ addsub_tile_bulk_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint3
     const unsigned long long epoch = lb.counters[2];
     const unsigned long long total = (unsigned long long)batch * tiles_per_op;
 
+    unsigned long long reserve = 0;   // thread 0: the ticket this block takes next
     auto issue = [&](int st, int k) {   // thread 0: start the copies of this block's k-th tile
-        const unsigned long long tk = blockIdx.x + (unsigned long long)k * gridDim.x;
+        const unsigned long long tk = reserve;
+        if (tk < total) reserve = atomicAdd(&lb.counters[0], 1ull);
         s_ticket[st] = tk;
         if (tk < total) {
             const unsigned long long op = tk / tiles_per_op, t = tk - op * tiles_per_op;
@@ -432,6 +438,7 @@ addsub_tile_bulk_kernel(const uint32_t *a, const uint32_t *b, uint32_t *s, uint3
         mbar_init(&s_bar[0], 1);
         mbar_init(&s_bar[1], 1);
         mbar_init_fence();
+        reserve = atomicAdd(&lb.counters[0], 1ull);
         issue(0, 0);
         issue(1, 1);
     }
@@ -555,15 +562,12 @@ static dot_status_t launch_tile(dot_ctx_t ctx, const dot_plan_t &pl, const uint3
                                         : (const void *)addsub_tile_bulk_kernel<SUB, 4>;
         if (cudaFuncSetAttribute(fb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return DOT_ECUDA;
-        // every block resident at once (the static schedule's look-back relies
-        // on it), and as few blocks as give every block the same number of
-        // tiles: a last round that only part of the blocks work on ends later
+        // one block per resident slot (tickets balance the tiles among them)
         const size_t cap = (size_t)ctx->num_sms * dot_blocks_per_sm(fb, DOT_TILE_THREADS, smem);
-        const size_t rounds = dot_ceil_div(tiles, cap);
-        const unsigned grid = (unsigned)dot_ceil_div(tiles, rounds);
+        const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
         void *args[] = {(void *)&a, (void *)&b, (void *)&s, (void *)&cout, (void *)&m, (void *)&batch,
                         (void *)&tpo, (void *)&lb};
-        const cudaError_t e = cudaLaunchCooperativeKernel(fb, dim3(grid), dim3(DOT_TILE_THREADS), args, smem, st);
+        const cudaError_t e = cudaLaunchKernel(fb, dim3(grid), dim3(DOT_TILE_THREADS), args, smem, st);
         return e == cudaSuccess ? DOT_OK : DOT_ECUDA;
     }
     const void *fn;
