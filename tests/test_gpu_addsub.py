@@ -91,6 +91,36 @@ def test_long_operands_80_pairs(D, op):
     assert_same(c, wc, f"{op} long carry")
 
 
+@pytest.mark.parametrize("op", ["add", "sub"])
+def test_long_operands_beside_another_kernel(D, op):
+    """The long-operand kernel on its own context and stream while a large
+    matmul holds SMs on another stream: not every block of the look-back
+    kernel is resident at once, and its tiles still resolve in ticket order."""
+    import torch
+    g = W.rng(41)
+    x, y = W.class_operands(g, "runs", 24, 1 << 17)
+    ctx = D.Context(torch.cuda.current_device())
+    try:
+        busy = torch.cuda.Stream()
+        mine = torch.cuda.Stream()
+        m1 = torch.randn(8192, 8192, device="cuda")
+        a, b = dev(x), dev(y)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(busy):
+            for _ in range(4):
+                m1 = m1 @ m1.T
+                m1 /= m1.abs().max()
+        with torch.cuda.stream(mine):
+            s, c = (D.add if op == "add" else D.sub)(a, b, ctx=ctx)
+        torch.cuda.synchronize()
+        assert ctx.check() == D.OK
+        ws, wc = want(op, x, y, threads=16)
+        assert_same(host(s), ws, f"{op} beside a matmul")
+        assert_same(host(c), wc, f"{op} carry beside a matmul")
+    finally:
+        ctx.close()
+
+
 def test_correctness_mix(D):
     d = W.correctness_mix()
     for op, (x, y) in (("add", (d["x"], d["y"])), ("sub", (d["a_sub"], d["b_sub"]))):
