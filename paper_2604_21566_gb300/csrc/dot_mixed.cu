@@ -16,12 +16,16 @@
 //      shapes are not held to the registers, and the occupancy, of the
 //      largest); each warp takes work items from its kernel's counter,
 //      heaviest buckets first (longest-processing-time order), and runs the
-//      multiply (column-block sums, Alg. 2) for the item's ops.  Small multiplies share a warp: a bucket fixes the
-//      run width T, and each op of the item takes a run of T lanes.  A bucket
-//      also fixes the columns per lane R, chosen so that an op's ceil(m / R)
-//      lanes fill most of its run: the 257..512-limb range is split at 384
-//      into R = 12 and R = 16 (with R = 16 alone a log-uniform size mix
-//      leaves 28% of those lanes idle, with the split about 15%).
+//      multiply (column-block sums, Alg. 2) for the item's ops.  Small
+//      multiplies share a warp: a bucket fixes the run width T, and each op
+//      of the item takes a run of T lanes.  A bucket also fixes the columns
+//      per lane R, chosen so that an op's ceil(m / R) lanes fill most of its
+//      run: above 256 limbs one bucket per 32 limbs, R = ceil(m / 32) = 9..16,
+//      so that 29 to 32 of the 32 lanes work; 129..256 limbs take R = 6, 7
+//      or 8.  A warp's time for one op goes as (ceil(m / R) + 1) R^2, so a
+//      wider R than the op needs costs as much as idle lanes: with R = 16
+//      and 12 for 257..512 limbs and R = 8 for 129..256, the 200k-op batch
+//      of the benchmark took 7% longer.
 // The six launches are captured once into a CUDA graph per context (the
 // add/sub kernel and the smaller products on one branch, the largest
 // products on another); later calls only update the graph's kernel-node
@@ -35,8 +39,15 @@
 #include "dot_warp_op.cuh"
 #include "dot_mul.cuh"
 
-// bucket ids, in processing order
-enum { BK_M16 = 0, BK_M12, BK_M8C, BK_M8B, BK_M8A, BK_M4, BK_ASL, BK_ASS, NBK };
+// bucket ids, in processing order (heaviest first): BK_R<R> runs one
+// multiply per warp with R columns per lane; BK_M8B / BK_M8A / BK_M4 run 2 /
+// 4 / 8 multiplies per warp; BK_ASL / BK_ASS are the add/sub ops
+enum {
+    BK_R16 = 0, BK_R15, BK_R14, BK_R13, BK_R12, BK_R11, BK_R10, BK_R9,   // 257..512 limbs
+    BK_R8, BK_R7, BK_R6,                                                  // 129..256 limbs
+    BK_M8B, BK_M8A, BK_M4, BK_ASL, BK_ASS, NBK
+};
+static_assert(NBK <= 16, "a slot keeps the bucket id in its top 4 bits");
 #define MIX_WARPS 4
 __host__ __device__ constexpr int cmax(int x, int y) { return x > y ? x : y; }
 #define MIX_MAX_OPS (1ull << 28)
@@ -81,9 +92,10 @@ __device__ __forceinline__ int bucket_of(uint32_t op, uint32_t m)
     if (m == 0) return -1;
     if (op != DOT_OP_MUL) return m > 128 ? BK_ASL : BK_ASS;
     if (m > DOT_MUL_MAX_LIMBS) return -3;
-    if (m > 384) return BK_M16;
-    if (m > 256) return BK_M12;
-    if (m > 128) return BK_M8C;
+    if (m > 256) return BK_R16 + (16 - (int)((m + 31) / 32));   // R = ceil(m / 32): ceil(m / R) <= 32
+    if (m > 224) return BK_R8;
+    if (m > 192) return BK_R7;
+    if (m > 128) return BK_R6;
     if (m > 64) return BK_M8B;
     if (m > 16) return BK_M8A;
     return BK_M4;
@@ -230,17 +242,20 @@ mixed_addsub(const dot_desc_t *desc, const uint32_t *order, const MixedMeta *met
 }
 
 // The products in two persistent kernels, each over a range of buckets
-// [LO, HI) with a work counter of its own: the 257..512-limb buckets (R = 16
-// and 12, the most registers) and the rest (R <= 8), so that the smaller
+// [LO, HI) with a work counter of its own: the 257..512-limb buckets (R = 9
+// to 16, the most registers) and the rest (R <= 8), so that the smaller
 // shapes run at the occupancy their registers allow instead of the largest
 // shape's.
+// Register caps: 3 blocks per SM for the 257..512-limb kernel (each shape
+// alone needs at most 164 registers, but the eight inlined together took 242
+// uncapped, which left 2 blocks per SM) and 4 for the other.
 template <int LO, int HI, int K>
-__global__ void __launch_bounds__(MIX_WARPS * 32)
+__global__ void __launch_bounds__(MIX_WARPS * 32, LO == BK_R16 ? 3 : 4)
 mixed_run(const dot_desc_t *desc, const uint32_t *order, MixedMeta *meta, const uint32_t *a,
           const uint32_t *b, uint32_t *r, uint32_t *carry)
 {
     // per-warp staging words: the largest shape of the kernel's buckets
-    constexpr int RW = LO == BK_M16 ? mix_region_words(16, 32)
+    constexpr int RW = LO == BK_R16 ? mix_region_words(16, 32)
                                     : cmax(cmax(mix_region_words(8, 32), mix_region_words(8, 16)),
                                            cmax(mix_region_words(8, 8), mix_region_words(4, 4)));
     __shared__ __align__(16) uint32_t smem[MIX_WARPS * RW];
@@ -258,12 +273,22 @@ mixed_run(const dot_desc_t *desc, const uint32_t *order, MixedMeta *meta, const 
             if (item >= meta->item_base[q]) bk = q;
         const uint32_t n = meta->n[bk], base = meta->base[bk];
         const uint32_t k0 = (uint32_t)(item - meta->item_base[bk]) * bucket_ops_per_item(bk);
-        if constexpr (LO == BK_M16) {
-            if (bk == BK_M16) mixed_mul_item<16, 32, RW>(desc, order, base, n, k0, a, b, r, carry, wsmem);
-            else mixed_mul_item<12, 32, RW>(desc, order, base, n, k0, a, b, r, carry, wsmem);
+        if constexpr (LO == BK_R16) {
+            switch (bk) {
+            case BK_R16: mixed_mul_item<16, 32, RW>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
+            case BK_R15: mixed_mul_item<15, 32, RW>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
+            case BK_R14: mixed_mul_item<14, 32, RW>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
+            case BK_R13: mixed_mul_item<13, 32, RW>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
+            case BK_R12: mixed_mul_item<12, 32, RW>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
+            case BK_R11: mixed_mul_item<11, 32, RW>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
+            case BK_R10: mixed_mul_item<10, 32, RW>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
+            default: mixed_mul_item<9, 32, RW>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
+            }
         } else {
             switch (bk) {
-            case BK_M8C: mixed_mul_item<8, 32, RW>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
+            case BK_R8: mixed_mul_item<8, 32, RW>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
+            case BK_R7: mixed_mul_item<7, 32, RW>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
+            case BK_R6: mixed_mul_item<6, 32, RW>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
             case BK_M8B: mixed_mul_item<8, 16, RW>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
             case BK_M8A: mixed_mul_item<8, 8, RW>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
             default: mixed_mul_item<4, 4, RW>(desc, order, base, n, k0, a, b, r, carry, wsmem); break;
@@ -281,8 +306,8 @@ mixed_run(const dot_desc_t *desc, const uint32_t *order, MixedMeta *meta, const 
         }
     }
 }
-#define MIX_RUN_WIDE mixed_run<BK_M16, BK_M8C, 0>
-#define MIX_RUN_NARROW mixed_run<BK_M8C, BK_ASL, 1>
+#define MIX_RUN_WIDE mixed_run<BK_R16, BK_R8, 0>
+#define MIX_RUN_NARROW mixed_run<BK_R8, BK_ASL, 1>
 
 // ------------------------------------------------------------------ host
 static MixedScratch *g_scratch_of(dot_ctx_t ctx);

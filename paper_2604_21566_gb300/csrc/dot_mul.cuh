@@ -57,13 +57,20 @@ __device__ __forceinline__ void cols_to_positional(const uint32_t (&s0)[R], cons
     }
 }
 
+// R words from shared memory: 16-byte loads when R % 4 == 0 (the caller's
+// address is then 16-byte aligned), one word at a time otherwise.
 template <int R>
 __device__ __forceinline__ void lds_vec(const uint32_t *p, uint32_t *v)
 {
+    if constexpr (R % 4 == 0) {
 #pragma unroll
-    for (int q = 0; q < R / 4; ++q) {
-        const uint4 t = reinterpret_cast<const uint4 *>(p)[q];
-        v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+        for (int q = 0; q < R / 4; ++q) {
+            const uint4 t = reinterpret_cast<const uint4 *>(p)[q];
+            v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < R; ++k) v[k] = p[k];
     }
 }
 
@@ -220,11 +227,12 @@ __device__ __forceinline__ void sqr_colsum_pair(const uint32_t *As, const uint32
 }
 
 // Copy limbs [t R, t R + R) of an m-limb row into shared memory (zeros past m).
+// 16-byte copies need R % 4 == 0 (block starts t R on 16-byte boundaries).
 template <int R>
 __device__ __forceinline__ void stage_row(const uint32_t *row, uint32_t *dst, int t, int m, bool vec)
 {
     const int l0 = t * R;
-    if (vec && l0 + R <= m) {
+    if (R % 4 == 0 && vec && l0 + R <= m) {
 #pragma unroll
         for (int q = 0; q < R / 4; ++q)
             reinterpret_cast<uint4 *>(dst + l0)[q] = ld_stream4(row + l0 + 4 * q);
@@ -237,7 +245,7 @@ __device__ __forceinline__ void stage_row(const uint32_t *row, uint32_t *dst, in
 template <int R>
 __device__ __forceinline__ void store_block(uint32_t *row, int pos, int len, const uint32_t (&v)[R], bool vec)
 {
-    if (vec && pos + R <= len) {
+    if (R % 4 == 0 && vec && pos + R <= len) {
 #pragma unroll
         for (int q = 0; q < R / 4; ++q)
             st_stream4(row + pos + 4 * q, make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));

@@ -93,6 +93,42 @@ def test_small_batches_every_bucket(D, seed):
         assert_same(r, wr, f"results k={k}")
 
 
+@pytest.mark.parametrize("cls", ["uniform", "runs", "ones", "max_pair"])
+def test_every_product_size(D, cls):
+    """One multiply of every size from 1 to 512 limbs, so that every bucket,
+    every boundary between buckets and every columns-per-lane shape (R = 4 to
+    16, odd R included) runs, twice over: once from operands packed back to
+    back (most rows not 16-byte aligned) and once with every row padded to a
+    multiple of 4 limbs; a few add/sub ops ride along."""
+    g = W.rng(800 + W.CLASSES.index(cls))
+    for padded in (False, True):
+        m = np.arange(1, 513, dtype=np.int64)
+        op = np.full(m.size, 2, dtype=np.uint32)
+        m = np.concatenate([m, [5, 300, 130]])
+        op = np.concatenate([op, np.array([0, 1, 0], dtype=np.uint32)])
+        if padded:
+            stored = (m + 3) // 4 * 4
+            a0, b0, off0 = W.ragged_uniform(g, stored, cls=cls)
+            # zero the padding: only the first m limbs of each row are operands
+            a, b = a0.copy(), b0.copy()
+            for k in range(m.size):
+                a[int(off0[k]) + int(m[k]):int(off0[k + 1])] = 0
+                b[int(off0[k]) + int(m[k]):int(off0[k + 1])] = 0
+            off = off0
+        else:
+            a, b, off = W.ragged_uniform(g, m, cls=cls)
+        r_len = np.where(op == 2, 2 * m, m)
+        r_len = (r_len + 3) // 4 * 4 if padded else r_len
+        r_off = np.concatenate([[0], np.cumsum(r_len)]).astype(np.uint64)
+        d = descriptors(op, m, off[:-1], r_off[:-1])
+        ctx = D.default_context()
+        r, c, st = run_mixed(D, ctx, d, a, b, r_off[-1])
+        assert st == D.OK
+        wr, wc = want_mixed(d, a, b, r_off[-1])
+        assert_same(c, wc, f"carries {cls} padded={padded}")
+        assert_same(r, wr, f"results {cls} padded={padded}")
+
+
 def test_bad_descriptors_reported(D):
     g = W.rng(9)
     sizes = np.array([8, 600, 8, 5, 0], dtype=np.int64)
