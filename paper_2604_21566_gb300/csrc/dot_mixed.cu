@@ -8,9 +8,10 @@
 //      ranges (and clears the counts for the next call);
 //   3. scatter: op indices are written bucket by bucket;
 //   4. add/sub: the additions and subtractions (Alg. 1), one warp per op
-//      over the two add/sub buckets, 64 warps per SM so that enough of them
-//      have loads in flight (as one item each behind the products, claimed
-//      one at a time, they ran at a seventh of the memory bandwidth);
+//      above 128 limbs and four ops per warp below, 32 warps per SM so that
+//      enough of them have loads in flight (as one item each behind the
+//      products, claimed one at a time, they ran at a seventh of the memory
+//      bandwidth);
 //   5. run: two persistent kernels for the products, one for the
 //      257..512-limb buckets and one for the rest (so that the smaller
 //      shapes are not held to the registers, and the occupancy, of the
@@ -210,14 +211,107 @@ __device__ __forceinline__ void mixed_mul_item(const dot_desc_t *desc, const uin
 #define MIX_AS_THREADS 256
 #define MIX_AS_BLOCKS_PER_SM 8
 
-// The add/sub ops, in bucket order (long ones first): warp k takes ops k,
-// k + W, ...; the next op's index and descriptor load while the current op
-// runs, so that only the op's own data loads sit on its critical path.
-__global__ void __launch_bounds__(MIX_AS_THREADS)
+// Four limbs of one lane for an add (sub false) or a subtract (sub true),
+// the op chosen at run time: the short-op path packs adds and subtracts into
+// one warp.  Same phases as Segment<SUB, 4> (dot_internal.cuh).
+struct SegAS {
+    uint32_t r[4];
+    uint32_t gm, pm;
+    __device__ __forceinline__ void phase12(const uint32_t (&x)[4], const uint32_t (&y)[4], bool sub)
+    {
+        gm = 0;
+        pm = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            r[i] = sub ? x[i] - y[i] : x[i] + y[i];
+            gm |= (uint32_t)(sub ? x[i] < y[i] : r[i] < x[i]) << i;
+            pm |= (uint32_t)(sub ? x[i] == y[i] : r[i] == DOT_FULL) << i;
+        }
+    }
+    __device__ __forceinline__ uint32_t g() const { return (((gm << 1) + pm) >> 4) & 1u; }
+    __device__ __forceinline__ uint32_t p() const { return pm == 0xfu; }
+    // carry (borrow) into limb j of the four, 0 <= j <= 4, for carry-in cin
+    // (bit j of the carry mask that apply() uses)
+    __device__ __forceinline__ uint32_t carry_at(uint32_t cin, int j) const
+    {
+        return (((((gm << 1) | cin) + pm) ^ pm) >> j) & 1u;
+    }
+    __device__ __forceinline__ void apply(uint32_t cin, bool sub)
+    {
+        const uint32_t cm = (((gm << 1) | cin) + pm) ^ pm;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t c = (cm >> i) & 1u;
+            r[i] = sub ? r[i] - c : r[i] + c;
+        }
+    }
+};
+
+// Add/sub ops of at most 128 limbs, four per warp: run g = lane / 8 takes
+// op 4 i + g of the short bucket, and lane t = lane % 8 of the run holds limbs
+// 32 k + 4 t .. 32 k + 4 t + 3 of its chunk k < 4, so one chunk of 32 limbs is
+// one run of the warp's ballot lookahead and all of an op's loads are in
+// flight at once (one op per warp left most lanes idle: these ops average
+// about 36 limbs).  Limbs past m read as 0 and are not stored; the carry
+// (borrow) out of limb m - 1 is read off the lane that holds it.
+__device__ __forceinline__ void mixed_addsub_short(const dot_desc_t *desc, const uint32_t *order, uint32_t base,
+                                                   uint32_t n, size_t item, const uint32_t *a, const uint32_t *b,
+                                                   uint32_t *r, uint32_t *carry)
+{
+    const int lane = (int)lane_id();
+    const int grp = lane >> 3, t = lane & 7;
+    const size_t idx = item * 4 + (size_t)grp;
+    const bool valid = idx < n;
+    uint32_t op = 0;
+    dot_desc_t d{};
+    if (valid) {
+        op = order[base + idx];
+        d = desc[op];
+    }
+    const uint32_t m = valid ? d.m : 0u;
+    const bool sub = d.op == DOT_OP_SUB;
+    const uint32_t *ar = a + d.a_off, *br = b + d.b_off;
+    uint32_t x[4][4], y[4][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t li = 32u * k + 4u * t + i;
+            x[k][i] = li < m ? ld_stream1(ar + li) : 0u;
+            y[k][i] = li < m ? ld_stream1(br + li) : 0u;
+        }
+    uint32_t cin = 0, fin = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t l0 = 32u * k + 4u * t;
+        const bool on = l0 < m;
+        SegAS sg;
+        sg.phase12(x[k], y[k], sub);
+        WarpCarry wc;
+        wc.resolve(on ? sg.g() : 0u, on ? sg.p() : 0u, t == 0 ? cin : 0u, 0x01010101u, 0x80808080u);
+        const uint32_t c = wc.carry_in(lane);
+        if (on && m - 1 < l0 + 4) fin = sg.carry_at(c, (int)(m - l0));   // limb m - 1 is one of these four
+        sg.apply(c, sub);
+        uint32_t *rr = r + d.r_off;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (l0 + i < m) st_stream1(rr + l0 + i, sg.r[i]);
+        cin = wc.carry_out((lane & ~7) | 7);   // out of the run's chunk: into its next chunk
+    }
+    const int src = (grp << 3) | (int)(((m - 1) & 31u) >> 2);
+    fin = __shfl_sync(DOT_FULL, fin, src);
+    if (valid && t == 0) carry[op] = fin;
+}
+
+// The add/sub ops: the long bucket first, warp k taking ops k, k + W, ...
+// (the next op's index and descriptor load while the current op runs, so that
+// only the op's own data loads sit on its critical path), then the short
+// bucket four ops per warp.
+__global__ void __launch_bounds__(MIX_AS_THREADS, 4)
 mixed_addsub(const dot_desc_t *desc, const uint32_t *order, const MixedMeta *meta, const uint32_t *a,
              const uint32_t *b, uint32_t *r, uint32_t *carry)
 {
-    const uint32_t n = meta->n[BK_ASL] + meta->n[BK_ASS], base = meta->base[BK_ASL];
+    const uint32_t n = meta->n[BK_ASL], base = meta->base[BK_ASL];
     const size_t wg = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const size_t nw = ((size_t)gridDim.x * blockDim.x) >> 5;
     size_t k = wg;
@@ -239,6 +333,9 @@ mixed_addsub(const dot_desc_t *desc, const uint32_t *order, const MixedMeta *met
         else
             addsub_warp_op<false>(a + dc.a_off, b + dc.b_off, r + dc.r_off, dc.m, carry + cur, dc.m, 0u);
     }
+    const uint32_t ns = meta->n[BK_ASS], bs = meta->base[BK_ASS];
+    const size_t items = ((size_t)ns + 3) / 4;
+    for (size_t it = wg; it < items; it += nw) mixed_addsub_short(desc, order, bs, ns, it, a, b, r, carry);
 }
 
 // The products in two persistent kernels, each over a range of buckets
